@@ -1,0 +1,83 @@
+"""Pins of the seeded input generators and of the droplet measurements (CPU only)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import measure, model as m
+from workloads import configs
+from workloads.droplets import place_droplets, phi_field, composition_fields
+from workloads.rng import SplitMix64
+
+
+def test_splitmix64_reference_vectors():
+    # outputs of the published splitmix64 reference for seeds 0 and 1234567
+    r = SplitMix64(0)
+    assert [r.next_u64() for _ in range(3)] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    r = SplitMix64(1234567)
+    assert [r.next_u64() for _ in range(3)] == [6457827717110365317, 3203168211198807973, 9817491932198370423]
+    u = SplitMix64(5).uniform()
+    assert 0.0 <= u < 1.0 and (u * 2 ** 53) == int(u * 2 ** 53)
+
+
+@pytest.mark.parametrize("walls", [(False, False, False), (False, False, True)])
+def test_droplet_placement_constraints(walls):
+    shape = (40, 36, 44)
+    W = 3.0
+    centres, radii = place_droplets(shape, 0.08, 3.0, 6.0, W, seed=11, walls=walls)
+    nz, ny, nx = shape
+    ext = np.array([nx, ny, nz], dtype=float)
+    vol = (4.0 / 3.0 * math.pi * radii ** 3).sum()
+    assert vol >= 0.08 * nx * ny * nz
+    assert np.all((radii >= 3.0) & (radii <= 6.0))
+    for i in range(len(radii)):
+        for j in range(i):
+            d = centres[i] - centres[j]
+            for ax in range(3):
+                if not walls[ax]:
+                    d[ax] -= ext[ax] * round(d[ax] / ext[ax])
+            assert np.linalg.norm(d) >= radii[i] + radii[j] + W
+        if walls[2]:
+            assert centres[i, 2] + 0.5 - radii[i] >= W / 2
+            assert ext[2] - 0.5 - centres[i, 2] - radii[i] >= W / 2
+    again = place_droplets(shape, 0.08, 3.0, 6.0, W, seed=11, walls=walls)
+    assert np.array_equal(again[0], centres) and np.array_equal(again[1], radii)
+
+
+def test_fields_and_measurements_on_known_spheres():
+    shape = (48, 48, 48)
+    W = 3.0
+    centres = np.array([[12.3, 14.1, 13.0], [34.0, 33.2, 30.7], [36.5, 10.0, 38.0]])
+    radii = np.array([7.0, 9.0, 6.0])
+    phi = phi_field(shape, centres, radii, W)
+    assert float(phi.max()) <= 1.0 and float(phi.min()) >= 0.0
+    # the tanh of Eq. 13 at the centre of the largest sphere, and (1 + tanh(2r/W))/2 at r from a surface
+    c = np.round(centres[1]).astype(int)
+    d = float(np.linalg.norm(c - centres[1]))
+    assert abs(float(phi[c[2], c[1], c[0]]) - m.tanh_profile(9.0 - d, W)) < 1e-12
+    R, n = measure.mean_radius(phi.numpy(), W)
+    assert n == 3
+    want = math.sqrt((4 * math.pi * (radii ** 2)).sum() / (4 * math.pi * 3))
+    assert abs(R / want - 1) < 0.03
+    cA, cB = composition_fields(phi, ((0.3, 0.3), (0.4, 0.4)), 0.02)
+    inside = phi >= 0.5
+    assert torch.all(cA[inside] == 0.4) and torch.allclose(cA[~inside], torch.full_like(cA[~inside], 0.302),
+                                                           rtol=0, atol=1e-15)
+
+
+def test_periodic_droplet_counts_once():
+    shape = (32, 32, 32)
+    phi = phi_field(shape, np.array([[1.0, 16.0, 16.0]]), np.array([6.0]), 3.0)
+    assert measure.count_droplets(phi.numpy()) == 1
+    assert measure.count_droplets(phi.numpy(), walls=(True, False, False)) == 2
+
+
+def test_configs_build():
+    p, fields = configs.ripening(shape=(24, 24, 24))
+    phi, cA, cB = fields()
+    assert phi.shape == p.shape and cA.dtype == torch.float64
+    p, fields = configs.diffusion_couple(nx=32, ny=2)
+    phi, cA, cB = fields()
+    assert phi.shape == (1, 2, 32)
+    assert float(cA[0, 0, 0]) == 0.55 and float(cB[0, 0, -1]) == 0.25
