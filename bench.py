@@ -1,0 +1,312 @@
+"""Throughput of the fused coupled lattice Boltzmann step on one GB300 (or N replicas).
+
+Workload: 512^3 lattice, D3Q19 flow + D3Q7 phi, c^A, c^B, FP32 population storage,
+half-way bounce-back walls at the z ends, periodic in x and y, seeded droplets at
+volume fraction 0.2 with radii in [6, 16] (seed 3). One "step" is one coupled time
+step of the whole lattice (the phi pass of the capillary stencil plus the fused
+collide-and-stream kernel). The 21.5 GB state is far larger than the 129 MB L2, so
+no flush is needed between timed steps.
+
+Prints one JSON line. --impl reference times the FP64 CPU oracle instead (the
+reference arm of this method), on a bounded slab of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coupled-step MLUPS at 512^3 + % HBM roofline; FP16-store and adjoint vs FP32"
+N = 512
+ALG_BYTES_PER_NODE = {"f32": 320.0, "f16": 168.0, "bf16": 168.0, "f64": 640.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=N)
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample-planes", type=int, default=16)
+    ap.add_argument("--cpu-sample-steps", type=int, default=6)
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_workload(n, device, storage="f32"):
+    from workloads import configs
+    p, fields = configs.sedimentation(n=n, storage=storage)
+    phi0, cA0, cB0 = fields(device=device)
+    return p, fields, (phi0, cA0, cB0)
+
+
+def cpu_baseline(init_fields, p, planes, steps):
+    """The FP64 oracle, as it stands, on a z-slab of the same initial fields."""
+    import torch
+    from oracle.lbm import OracleLBM
+    z0 = p.nz // 2 - planes // 2
+    sl = [t[z0:z0 + planes].detach().cpu().double() for t in init_fields]
+    q = p.with_(nz=planes)
+    o = OracleLBM(q)
+    o.init(*sl)
+    o.step(1)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    mlups = q.nodes * steps / dt / 1e6
+    return {"value": mlups, "unit": "MLUPS", "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"{q.nx}x{q.ny}x{planes} slab (z {z0}..{z0 + planes - 1}) of the 512^3 initial fields, "
+                      f"walls at the slab ends, {steps} steps after 1 untimed, {dt:.1f} s"}
+
+
+def time_device(sim, steps, warmup, dist):
+    """Device-timed K steps with CUDA events on the simulation's stream, plus per-kernel
+    event timing of the same region from the library."""
+    import torch
+    sim.step(warmup)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    sim.profile_begin(steps)
+    start.record(sim.stream)
+    sim.step(steps)
+    stop.record(sim.stream)
+    torch.cuda.synchronize()
+    ms = start.elapsed_time(stop)
+    ms_phi, ms_step, nprof = sim.profile_end()
+    if dist:
+        import torch.distributed as td
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        td.all_reduce(t, op=td.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, ms_phi / max(nprof, 1), ms_step / max(nprof, 1)
+
+
+def run_e2e(p, init, steps, device):
+    """Same metric through the public API with host buffers: pinned host inputs copied
+    in, init, K steps, phi and mu copied out, FP64 sums read back, all in the timed region."""
+    import torch
+    from paper_2409_03401_gb300 import Simulation
+    host = [t.cpu().pin_memory() for t in init]       # staged on the host before the timed region
+    out_host = {k: torch.empty(p.shape, dtype=torch.float32).pin_memory() for k in ("phi", "muA", "muB")}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    dev = [t.to(device, non_blocking=True) for t in host]
+    sim = Simulation(p, *dev, device=device)
+    sim.step(steps)
+    f = sim.fields(names=("phi", "muA", "muB"))
+    for k in out_host:
+        out_host[k].copy_(f[k], non_blocking=True)
+    sums = sim.sums()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    h2d = sum(t.numel() * t.element_size() for t in host)
+    d2h = sum(t.numel() * t.element_size() for t in out_host.values()) + 8 * len(sums)
+    del sim, dev, f
+    return {"value": p.nodes * steps / dt / 1e6, "unit": "MLUPS",
+            "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps,
+            "steps": steps, "seconds": dt}
+
+
+def gb300(args):
+    import torch
+    ws, rank, local = dist_env()
+    dist = None
+    if ws > 1:
+        import torch.distributed as td
+        td.init_process_group("nccl")
+        dist = td
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    from paper_2409_03401_gb300 import Simulation
+
+    p, fields_fn, init = make_workload(args.n, device)
+    sim = Simulation(p, *init, device=device)
+    peak, peak_kind = peaks()
+    with ClockSampler(local) as clk:
+        ms, ms_phi, ms_step = time_device(sim, args.steps, args.warmup, dist)
+    s = sim.sums()
+    nodes = p.nodes
+    value = ws * nodes * args.steps / (ms / 1e3) / 1e6
+    bytes_step = ALG_BYTES_PER_NODE["f32"] * nodes
+    achieved = bytes_step / (ms_step / 1e3) / 1e9
+    out = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{args.n}^3 coupled step: D3Q19 flow + D3Q7 phi/cA/cB, FP32 storage, "
+                               "walls at z ends, droplets 0.2 vol. frac., r in [6,16], seed 3",
+                   "lattice": [p.nx, p.ny, p.nz], "storage": "f32",
+                   "l2": "state 21.5 GB >> 129 MB L2, no flush", "parallelism": f"replicas x{ws}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "step_kernel<float, D3Q7, flow> (fused collide+stream)",
+                     "alg_bytes_per_launch": bytes_step, "ms_per_launch": ms_step,
+                     "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
+                     "whole_step_frac": bytes_step / (ms / args.steps / 1e3) / 1e9 / peak,
+                     "phi_pass_ms": ms_phi},
+        "gpu_launches": sim.kernels_per_step * args.steps,
+        "clocks": clk.summary(),
+        "diagnostics": {"nonfinite": s["nonfinite"], "sum_cA": s["cA"], "umax": s["umax"]},
+    }
+    del sim
+    torch.cuda.synchronize()
+
+    if not args.no_variants:
+        var = {}
+        for storage in ("f16", "bf16"):
+            q = p.with_(storage=storage)
+            v = Simulation(q, *init, device=device)
+            vms, _, vstep = time_device(v, max(20, args.steps // 2), args.warmup, dist)
+            vs = max(20, args.steps // 2)
+            vb = ALG_BYTES_PER_NODE[storage] * nodes
+            var[storage] = {"value": ws * nodes * vs / (vms / 1e3) / 1e6, "unit": "MLUPS",
+                            "ms_per_step": vms / vs, "speedup_vs_f32": (ms / args.steps) / (vms / vs),
+                            "alg_bytes_per_node": ALG_BYTES_PER_NODE[storage],
+                            "roofline_frac": vb / (vstep / 1e3) / 1e9 / peak}
+            del v
+            torch.cuda.synchronize()
+        out["variants"] = var
+
+    if not args.no_e2e:
+        out["e2e"] = run_e2e(p, init, args.steps, device)
+
+    if rank == 0 and ws == 1:
+        out["cpu_baseline"] = cpu_baseline(init, p, args.cpu_sample_planes, args.cpu_sample_steps)
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import torch
+    from workloads import configs
+    from oracle.lbm import OracleLBM
+    p, fields_fn = configs.sedimentation(n=args.n)
+    # each reference "step" is one oracle step over a bounded slab of the same workload
+    planes = args.cpu_sample_planes
+    z0 = p.nz // 2 - planes // 2
+    q = p.with_(nz=planes)
+    o = OracleLBM(q)
+    o.init(*fields_fn(device="cpu", z_range=(z0, z0 + planes)))
+    steps = min(args.steps, 10)
+    o.step(min(args.warmup, 2))
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    value = q.nodes * steps / dt / 1e6
+    sample = (f"{q.nx}x{q.ny}x{planes} slab (z {z0}..{z0 + planes - 1}) of the {args.n}^3 initial fields, "
+              f"walls at the slab ends; {steps} timed steps (of {args.steps} asked) after "
+              f"{min(args.warmup, 2)} untimed")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws,
+           "steps": steps, "warmup": min(args.warmup, 2), "ms_per_step": dt / steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": f"{args.n}^3 coupled step (bounded slab sample), FP64 CPU oracle",
+                      "lattice": [q.nx, q.ny, q.nz]},
+           "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": torch.get_num_threads(),
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference(args)
+    else:
+        gb300(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,158 @@
+/*
+ * C-ABI of the GB300 (sm_103a) grand-potential phase-field lattice Boltzmann step.
+ *
+ * The method (Verdier, Cartalade, Plapp, "Grand-potential phase field simulations
+ * of droplet growth and sedimentation in a two-phase ternary fluid") couples, on
+ * one lattice, four BGK lattice Boltzmann equations:
+ *   g     - the Allen-Cahn phase field phi with its source S_phi   (§3.2, Eqs. 46-49, 35)
+ *   h^A,B - the compositions c^A, c^B; mu from the closure Eq. 33  (§3.3, Eqs. 50-52)
+ *   f     - incompressible flow with capillary + buoyancy forcing  (§3.1, Eqs. 36-45, 34)
+ * g, h^A, h^B use D2Q5 (2D) or D3Q7 (3D); f uses the D3Q19 set of the paper's table.
+ * One call of lbm_step advances every population set by one fused collide-and-stream
+ * pass over HBM with in-place AA-pattern streaming.
+ *
+ * Memory: every device buffer is allocated and owned by the caller (for instance a
+ * torch tensor); the library never allocates or frees device memory. The context is
+ * a small host object. All work is queued on the caller's CUDA stream; only
+ * lbm_reduce synchronises that stream.
+ *
+ * Errors: every entry point returns an lbm_status; nothing aborts, traps or exits.
+ * lbm_last_error gives a message for the last failure on a context.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = -1,       /* invalid argument: sizes, enum values, null pointers, alignment */
+    LBM_ERR_CUDA = -2,      /* a CUDA call failed; lbm_last_error has the CUDA message */
+    LBM_ERR_UNSTABLE = -3,  /* lbm_reduce found a non-finite value in the state */
+    LBM_ERR_STATE = -4      /* call out of order (e.g. adjoint on a flow lattice) */
+} lbm_status;
+
+typedef enum { LBM_D2Q5 = 0, LBM_D3Q7 = 1 } lbm_lattice;
+
+/* Storage type of the populations. Arithmetic is FP64 for LBM_F64 and FP32 otherwise.
+ * LBM_F16 / LBM_BF16 store every moving population as a 16-bit deviation from its
+ * lattice-weight reference, q_k = P_k / w_k - ref (f: ref 0 times f_scale; g: ref 1/2;
+ * h: ref 0 times 64); the three rest populations g_0, h^A_0, h^B_0 stay FP32. */
+typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16 = 2, LBM_BF16 = 3 } lbm_storage;
+
+/* Model parameters in lattice units (dx = dt = 1, rho_0 = 1), named as in the paper. */
+typedef struct lbm_params {
+    int32_t nx, ny, nz;      /* lattice extents; nz = 1 with LBM_D2Q5 */
+    int32_t lattice;         /* lbm_lattice of g, h^A, h^B */
+    int32_t flow;            /* 1: D3Q19 flow populations, capillary (Eq. 34) + buoyancy forcing */
+    int32_t storage;         /* lbm_storage */
+    int32_t wall_x;          /* 1: half-way bounce-back planes at x = -1/2 and nx - 1/2 */
+    int32_t wall_z;          /* 1: half-way bounce-back planes at z = -1/2 and nz - 1/2 */
+    int32_t source_off;      /* 1: S_phi = 0 (pure advection-diffusion of phi; test switch) */
+    int32_t reserved;        /* must be 0 */
+    double W;                /* interface width (Eq. 14) */
+    double lambda;           /* coupling constant lambda = K / H (§2.2) */
+    double M_phi;            /* scaled phase-field mobility, M_phi = W^2 / tau_phi */
+    double c_eq[2][2];       /* c_eq[pi][alpha]: equilibrium composition of phase pi, component alpha */
+    double M[2][2];          /* M[pi][alpha]: mobility of component alpha in phase pi (§2.3) */
+    double nu;               /* kinematic viscosity, tau_f = nu / c_s^2 (Eq. 36) */
+    double sigma;            /* surface tension in Eq. 34 */
+    double g[3];             /* buoyancy per unit phi: F_g = phi * g (§2.5, Delta rho g / rho_0) */
+    double f_scale;          /* 16-bit storage: scale of f_k / w_k (power of two recommended) */
+} lbm_params;
+
+/* Indices of lbm_fields outputs. */
+enum {
+    LBM_FIELD_PHI = 0, LBM_FIELD_MU_A, LBM_FIELD_MU_B, LBM_FIELD_C_A, LBM_FIELD_C_B,
+    LBM_FIELD_P, LBM_FIELD_UX, LBM_FIELD_UY, LBM_FIELD_UZ, LBM_FIELD_S,
+    LBM_NFIELDS
+};
+
+/* Indices of lbm_reduce outputs. */
+enum {
+    LBM_RED_PHI = 0,     /* sum phi (Eq. 49) */
+    LBM_RED_C_A,         /* sum c^A (Eq. 52), invariant */
+    LBM_RED_C_B,         /* sum c^B, invariant */
+    LBM_RED_P,           /* sum p_h (Eq. 40), invariant */
+    LBM_RED_S,           /* sum S_phi: the next step changes sum g by exactly this */
+    LBM_RED_UMAX,        /* max |u| (Eq. 41) */
+    LBM_RED_G,           /* sum of all g populations (= sum phi - sum S / 2) */
+    LBM_RED_NONFINITE,   /* number of nodes with a non-finite moment */
+    LBM_NRED
+};
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Bytes of the population state for these parameters (256-byte aligned planes). */
+size_t lbm_state_bytes(const lbm_params* p);
+
+/* Bytes of scratch the step needs beside the state: the phi field read by the
+ * capillary stencil (flow only) and the block partials of lbm_reduce. */
+size_t lbm_work_bytes(const lbm_params* p);
+
+/* Validate p, bind the caller's device buffers and CUDA stream (cudaStream_t passed as
+ * void*, NULL = legacy default stream), and write the initial populations at rest
+ * (§4.2.1): g = w phi0 - w S0/2, h = h^eq(c0, mu0) with mu0 from Eq. 33, f = f^eq at
+ * p_h = 0, u = 0 shifted by the initial forcing. d_phi0, d_cA0, d_cB0 are FP64 device
+ * arrays of nx*ny*nz values, x fastest; they are read during the call's kernel and may
+ * be freed once the stream has passed it. d_state (lbm_state_bytes) and d_work
+ * (lbm_work_bytes) must be 256-byte aligned and stay valid until lbm_destroy.
+ * On success *out receives a new context (time 0). */
+lbm_status lbm_init(const lbm_params* p, void* d_state, void* d_work,
+                    const double* d_phi0, const double* d_cA0, const double* d_cB0,
+                    void* stream, lbm_ctx** out);
+
+/* Bind buffers whose state was written earlier (checkpoint/resume): d_state must hold
+ * a state produced by this library for the same parameters at time t. No kernel runs. */
+lbm_status lbm_attach(const lbm_params* p, void* d_state, void* d_work, int64_t t,
+                      void* stream, lbm_ctx** out);
+
+/* Advance nsteps >= 0 coupled time steps (§3, one fused collide-and-stream kernel
+ * per step, plus the phi pass of the capillary stencil with flow). Asynchronous. */
+lbm_status lbm_step(lbm_ctx* ctx, int nsteps);
+
+/* Current time level (number of steps since lbm_init). */
+int64_t lbm_time(const lbm_ctx* ctx);
+
+/* Macroscopic fields of the current time level into caller device buffers:
+ * dst[LBM_NFIELDS] pointers, NULL for fields not wanted; each holds nx*ny*nz values,
+ * x fastest, in double for LBM_F64 and float otherwise. phi = sum g + S/2 (Eq. 49),
+ * mu by Eq. 33, c by Eq. 52, p by Eq. 40, u by Eq. 41 (0 without flow). Asynchronous. */
+lbm_status lbm_fields(lbm_ctx* ctx, void* const* dst);
+
+/* FP64 global diagnostics of the current time level into host memory out[LBM_NRED].
+ * Synchronises the stream. Returns LBM_ERR_UNSTABLE if a moment is not finite. */
+lbm_status lbm_reduce(lbm_ctx* ctx, double* out);
+
+/* Kernel timing on the context's stream. lbm_profile_begin(ctx, max_steps) creates
+ * 3 * max_steps CUDA events (host-side driver objects, no device memory); each of the
+ * next max_steps steps records one event before, between and after its kernels.
+ * lbm_profile_end synchronises the stream and writes out[0] = total ms of the phi
+ * passes, out[1] = total ms of the fused step kernels, out[2] = steps timed, then
+ * destroys the events. */
+lbm_status lbm_profile_begin(lbm_ctx* ctx, int max_steps);
+lbm_status lbm_profile_end(lbm_ctx* ctx, double* out);
+
+/* Number of kernels one lbm_step(ctx, 1) launches (2 with flow, else 1). */
+int lbm_kernels_per_step(const lbm_ctx* ctx);
+
+/* Release the context (host memory only; device buffers remain the caller's). */
+lbm_status lbm_destroy(lbm_ctx* ctx);
+
+/* Message of the last error on ctx (or of the last failed lbm_init/lbm_attach when
+ * ctx is NULL). Never NULL. */
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+/* Build and device information, for diagnostics: "sm_103a ..." */
+const char* lbm_build_info(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_GB300_H */

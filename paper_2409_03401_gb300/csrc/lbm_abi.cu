@@ -1,0 +1,339 @@
+// C-ABI entry points (include/lbm.h): validation, buffer layout, launch sequencing.
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_launch.h"
+
+using lbm::DevParams;
+using lbm::StateView;
+
+namespace {
+
+constexpr long long kAlign = 256;
+constexpr int kRedBlocks = 1216;   // 152 SMs x 8 blocks of 256 threads
+
+long long round_up(long long v, long long a) { return (v + a - 1) / a * a; }
+
+int scalar_q(int lattice) { return lattice == LBM_D2Q5 ? 5 : 7; }
+size_t storage_size(int s) { return s == LBM_F64 ? 8 : (s == LBM_F32 ? 4 : 2); }
+bool is16(int s) { return s == LBM_F16 || s == LBM_BF16; }
+
+thread_local std::string g_last_error = "no error";
+
+struct Layout {
+    long long n = 0, plane = 0;
+    size_t state = 0, work = 0;
+    size_t off_f = 0, off_g = 0, off_hA = 0, off_hB = 0, off_rest = 0;
+    size_t off_phi = 0, off_partials = 0, off_out = 0;
+};
+
+const char* check_params(const lbm_params* p) {
+    if (!p) return "params is NULL";
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return "lattice extents must be >= 1";
+    if (p->ny > 65535 || p->nz > 65535) return "ny and nz must be <= 65535";
+    if (p->lattice != LBM_D2Q5 && p->lattice != LBM_D3Q7) return "lattice must be LBM_D2Q5 or LBM_D3Q7";
+    if (p->lattice == LBM_D2Q5 && p->nz != 1) return "LBM_D2Q5 needs nz == 1";
+    if (p->flow != 0 && p->flow != 1) return "flow must be 0 or 1";
+    if (p->flow && p->lattice != LBM_D3Q7) return "flow needs the 3D lattice (LBM_D3Q7 scalars, D3Q19 flow)";
+    if (p->storage < LBM_F64 || p->storage > LBM_BF16) return "storage must be one of lbm_storage";
+    if (p->reserved != 0) return "reserved must be 0";
+    if (!(p->W > 0)) return "W must be > 0";
+    if (!(p->M_phi > 0)) return "M_phi must be > 0";
+    for (int ph = 0; ph < 2; ++ph)
+        for (int a = 0; a < 2; ++a)
+            if (!(p->M[ph][a] > 0)) return "mobilities M must be > 0";
+    if (p->flow && !(p->nu > 0)) return "nu must be > 0 with flow";
+    if (is16(p->storage) && p->f_scale < 0) return "f_scale must be >= 0 (0 selects 1024)";
+    return nullptr;
+}
+
+Layout layout_of(const lbm_params* p) {
+    Layout L;
+    L.n = (long long)p->nx * p->ny * p->nz;
+    L.plane = round_up(L.n, 128);
+    const size_t es = storage_size(p->storage);
+    const size_t pb = (size_t)L.plane * es;
+    const int Q = scalar_q(p->lattice);
+    size_t o = 0;
+    L.off_f = o;  o += p->flow ? 19 * pb : 0;
+    L.off_g = o;  o += Q * pb;
+    L.off_hA = o; o += Q * pb;
+    L.off_hB = o; o += Q * pb;
+    L.off_rest = o; o += is16(p->storage) ? 3 * (size_t)L.plane * sizeof(float) : 0;
+    L.state = round_up(o, kAlign);
+    const size_t real = p->storage == LBM_F64 ? 8 : 4;
+    size_t w = 0;
+    L.off_phi = w;      w += p->flow ? round_up((size_t)L.plane * real, kAlign) : 0;
+    L.off_partials = w; w += round_up((size_t)kRedBlocks * LBM_NRED * sizeof(double), kAlign);
+    L.off_out = w;      w += round_up(LBM_NRED * sizeof(double), kAlign);
+    L.work = w;
+    return L;
+}
+
+DevParams dev_params(const lbm_params* p, const Layout& L) {
+    DevParams d{};
+    d.nx = p->nx; d.ny = p->ny; d.nz = p->nz;
+    d.wall_x = p->wall_x != 0; d.wall_z = p->wall_z != 0; d.source_off = p->source_off != 0;
+    d.n = L.n; d.plane = L.plane;
+    d.W = p->W; d.lam = p->lambda;
+    d.kphi = p->M_phi / (p->W * p->W);
+    const double cs2 = p->lattice == LBM_D2Q5 ? 1.0 / 3.0 : 0.25;
+    d.inv_cs2 = 1.0 / cs2;
+    for (int a = 0; a < 2; ++a) {
+        d.c0[a] = p->c_eq[0][a];
+        d.c1[a] = p->c_eq[1][a];
+        d.dc[a] = p->c_eq[1][a] - p->c_eq[0][a];
+        d.M0[a] = p->M[0][a];
+        d.M1[a] = p->M[1][a];
+    }
+    d.om_g = 1.0 / (p->M_phi / cs2 + 0.5);
+    d.om_f = p->flow ? 1.0 / (p->nu * 3.0 + 0.5) : 0.0;
+    d.sw15 = 1.5 * p->sigma * p->W;
+    d.inv_W2 = 1.0 / (p->W * p->W);
+    for (int i = 0; i < 3; ++i) d.g[i] = p->g[i];
+    d.f_scale = p->f_scale > 0 ? p->f_scale : 1024.0;
+    d.inv_f_scale = 1.0 / d.f_scale;
+    return d;
+}
+
+}  // namespace
+
+struct lbm_ctx {
+    lbm_params p;
+    Layout L;
+    DevParams dp;
+    StateView st;
+    char* work;
+    cudaStream_t stream;
+    int64_t t;
+    std::string err;
+    std::vector<cudaEvent_t> ev;   // profiling: 3 events per timed step
+    int prof_max = 0, prof_n = 0;
+};
+
+namespace {
+
+lbm_status fail(lbm_ctx* c, lbm_status s, const std::string& msg) {
+    if (c) c->err = msg; else g_last_error = msg;
+    return s;
+}
+
+lbm_status cuda_check(lbm_ctx* c, const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(c, LBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+#define LBM_DISPATCH(STORAGE, FN, ...)                                         \
+    switch (STORAGE) {                                                         \
+        case LBM_F64: lbm::FN##_f64(__VA_ARGS__); break;                       \
+        case LBM_F32: lbm::FN##_f32(__VA_ARGS__); break;                       \
+        case LBM_F16: lbm::FN##_f16(__VA_ARGS__); break;                       \
+        default: lbm::FN##_bf16(__VA_ARGS__); break;                           \
+    }
+
+__global__ void reduce_final(const double* __restrict__ partials, int nblocks, double* __restrict__ out) {
+    __shared__ double sm[LBM_NRED][256];
+    for (int i = 0; i < LBM_NRED; ++i) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+            double u = partials[(long long)b * LBM_NRED + i];
+            v = (i == LBM_RED_UMAX) ? fmax(v, u) : v + u;
+        }
+        sm[i][threadIdx.x] = v;
+    }
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+            for (int i = 0; i < LBM_NRED; ++i)
+                sm[i][threadIdx.x] = (i == LBM_RED_UMAX) ? fmax(sm[i][threadIdx.x], sm[i][threadIdx.x + s])
+                                                         : sm[i][threadIdx.x] + sm[i][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x < LBM_NRED) out[threadIdx.x] = sm[threadIdx.x][0];
+}
+
+lbm_status bind(const lbm_params* p, void* d_state, void* d_work, void* stream, lbm_ctx** out) {
+    if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (const char* m = check_params(p)) return fail(nullptr, LBM_ERR_ARG, m);
+    if (!d_state || !d_work) return fail(nullptr, LBM_ERR_ARG, "state and work buffers must be non-NULL");
+    if (((uintptr_t)d_state % kAlign) || ((uintptr_t)d_work % kAlign))
+        return fail(nullptr, LBM_ERR_ARG, "state and work buffers must be 256-byte aligned");
+    lbm_ctx* c = new (std::nothrow) lbm_ctx();
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "host allocation of the context failed");
+    c->p = *p;
+    c->L = layout_of(p);
+    c->dp = dev_params(p, c->L);
+    char* s = static_cast<char*>(d_state);
+    c->st.f = p->flow ? s + c->L.off_f : nullptr;
+    c->st.g = s + c->L.off_g;
+    c->st.hA = s + c->L.off_hA;
+    c->st.hB = s + c->L.off_hB;
+    c->st.rest = is16(p->storage) ? reinterpret_cast<float*>(s + c->L.off_rest) : nullptr;
+    c->work = static_cast<char*>(d_work);
+    c->stream = static_cast<cudaStream_t>(stream);
+    c->t = 0;
+    c->err = "no error";
+    *out = c;
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lbm_state_bytes(const lbm_params* p) {
+    if (check_params(p)) return 0;
+    return layout_of(p).state;
+}
+
+size_t lbm_work_bytes(const lbm_params* p) {
+    if (check_params(p)) return 0;
+    return layout_of(p).work;
+}
+
+lbm_status lbm_init(const lbm_params* p, void* d_state, void* d_work, const double* d_phi0,
+                    const double* d_cA0, const double* d_cB0, void* stream, lbm_ctx** out) {
+    if (!d_phi0 || !d_cA0 || !d_cB0) {
+        if (out) *out = nullptr;
+        return fail(nullptr, LBM_ERR_ARG, "initial fields must be non-NULL device pointers");
+    }
+    lbm_status s = bind(p, d_state, d_work, stream, out);
+    if (s != LBM_OK) return s;
+    lbm_ctx* c = *out;
+    cudaGetLastError();
+    LBM_DISPATCH(c->p.storage, launch_init, c->dp, c->st, c->p.lattice, c->p.flow != 0, d_phi0, d_cA0, d_cB0,
+                 c->stream);
+    s = cuda_check(c, "init kernel launch");
+    if (s != LBM_OK) {
+        g_last_error = c->err;
+        delete c;
+        *out = nullptr;
+    }
+    return s;
+}
+
+lbm_status lbm_attach(const lbm_params* p, void* d_state, void* d_work, int64_t t, void* stream, lbm_ctx** out) {
+    if (t < 0) {
+        if (out) *out = nullptr;
+        return fail(nullptr, LBM_ERR_ARG, "t must be >= 0");
+    }
+    lbm_status s = bind(p, d_state, d_work, stream, out);
+    if (s == LBM_OK) (*out)->t = t;
+    return s;
+}
+
+lbm_status lbm_step(lbm_ctx* c, int nsteps) {
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+    if (nsteps < 0) return fail(c, LBM_ERR_ARG, "nsteps must be >= 0");
+    cudaGetLastError();
+    for (int i = 0; i < nsteps; ++i) {
+        const bool odd = (c->t & 1) != 0;
+        const bool timed = c->prof_n < c->prof_max;
+        cudaEvent_t* e = timed ? &c->ev[3 * c->prof_n] : nullptr;
+        if (timed) cudaEventRecord(e[0], c->stream);
+        if (c->p.flow) {
+            LBM_DISPATCH(c->p.storage, launch_phi, c->dp, c->st, c->p.lattice, odd, c->work + c->L.off_phi,
+                         c->stream);
+        }
+        if (timed) cudaEventRecord(e[1], c->stream);
+        LBM_DISPATCH(c->p.storage, launch_step, c->dp, c->st, c->p.lattice, c->p.flow != 0, odd,
+                     c->work + c->L.off_phi, c->stream);
+        if (timed) { cudaEventRecord(e[2], c->stream); c->prof_n += 1; }
+        c->t += 1;
+    }
+    return cuda_check(c, "step kernel launch");
+}
+
+lbm_status lbm_profile_begin(lbm_ctx* c, int max_steps) {
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+    if (max_steps < 0 || max_steps > 1000000) return fail(c, LBM_ERR_ARG, "max_steps out of range");
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    c->ev.assign(3 * (size_t)max_steps, nullptr);
+    for (auto& e : c->ev) {
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            c->prof_max = c->prof_n = 0;
+            return cuda_check(c, "profile event create");
+        }
+    }
+    c->prof_max = max_steps;
+    c->prof_n = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_profile_end(lbm_ctx* c, double* out) {
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+    if (!out) return fail(c, LBM_ERR_ARG, "out is NULL");
+    cudaError_t err = cudaStreamSynchronize(c->stream);
+    if (err != cudaSuccess) return fail(c, LBM_ERR_CUDA, std::string("profile sync: ") + cudaGetErrorString(err));
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < c->prof_n; ++i) {
+        float m0 = 0.f, m1 = 0.f;
+        cudaEventElapsedTime(&m0, c->ev[3 * i], c->ev[3 * i + 1]);
+        cudaEventElapsedTime(&m1, c->ev[3 * i + 1], c->ev[3 * i + 2]);
+        a += m0;
+        b += m1;
+    }
+    out[0] = a; out[1] = b; out[2] = c->prof_n;
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    c->ev.clear();
+    c->prof_max = c->prof_n = 0;
+    return cuda_check(c, "profile events");
+}
+
+int lbm_kernels_per_step(const lbm_ctx* c) { return c ? (c->p.flow ? 2 : 1) : 0; }
+
+int64_t lbm_time(const lbm_ctx* c) { return c ? c->t : -1; }
+
+lbm_status lbm_fields(lbm_ctx* c, void* const* dst) {
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+    if (!dst) return fail(c, LBM_ERR_ARG, "dst is NULL");
+    lbm::FieldPtrs fp;
+    for (int i = 0; i < LBM_NFIELDS; ++i) fp.p[i] = dst[i];
+    cudaGetLastError();
+    const bool odd = (c->t & 1) != 0;
+    LBM_DISPATCH(c->p.storage, launch_fields, c->dp, c->st, c->p.lattice, c->p.flow != 0, odd,
+                 c->work + c->L.off_phi, fp, c->stream);
+    return cuda_check(c, "fields kernel launch");
+}
+
+lbm_status lbm_reduce(lbm_ctx* c, double* out) {
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+    if (!out) return fail(c, LBM_ERR_ARG, "out is NULL");
+    cudaGetLastError();
+    const bool odd = (c->t & 1) != 0;
+    double* partials = reinterpret_cast<double*>(c->work + c->L.off_partials);
+    double* dout = reinterpret_cast<double*>(c->work + c->L.off_out);
+    LBM_DISPATCH(c->p.storage, launch_reduce, c->dp, c->st, c->p.lattice, c->p.flow != 0, odd,
+                 c->work + c->L.off_phi, partials, kRedBlocks, c->stream);
+    reduce_final<<<1, 256, 0, c->stream>>>(partials, kRedBlocks, dout);
+    lbm_status s = cuda_check(c, "reduce kernel launch");
+    if (s != LBM_OK) return s;
+    cudaError_t e = cudaMemcpyAsync(out, dout, LBM_NRED * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(c, LBM_ERR_CUDA, std::string("reduce copy: ") + cudaGetErrorString(e));
+    if (out[LBM_RED_NONFINITE] != 0.0)
+        return fail(c, LBM_ERR_UNSTABLE, "non-finite moments in the state (unstable run)");
+    return LBM_OK;
+}
+
+lbm_status lbm_destroy(lbm_ctx* c) {
+    if (c) for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    delete c;
+    return LBM_OK;
+}
+
+const char* lbm_last_error(const lbm_ctx* c) {
+    return c ? c->err.c_str() : g_last_error.c_str();
+}
+
+const char* lbm_build_info(void) {
+    return "gplbm sm_103a: AA-pattern fused collide-stream; storage f64/f32/f16/bf16; D2Q5/D3Q7 + D3Q19";
+}
+
+}  // extern "C"

@@ -1,0 +1,211 @@
+// Device-side building blocks of the coupled step: lattice tables, storage codecs,
+// AA-pattern addressing and the per-node physics of §3. Included by the per-storage
+// translation units; nothing here launches work.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// ------------------------------------------------------------------------------------
+// Parameters as the kernels see them (derived once on the host from lbm_params).
+struct DevParams {
+    int nx, ny, nz;
+    int wall_x, wall_z, source_off;
+    long long n;          // nodes
+    long long plane;      // elements between two population planes (n rounded up)
+    double W, lam;
+    double kphi;          // M_phi / W^2 = 1 / tau_phi (§2.2)
+    double c0[2], c1[2];  // c_0^eq, c_1^eq per component
+    double dc[2];         // c_1^eq - c_0^eq
+    double om_g;          // 1 / (M_phi / c_s^2 + 1/2)  (Eq. 46 with M_phi = tau_g c_s^2)
+    double M0[2], M1[2];  // mobilities of phase 0 and 1 per component (§2.3)
+    double inv_cs2;       // 1 / c_s^2 of the scalar lattice
+    double om_f;          // 1 / (nu / c_s^2 + 1/2)  (Eq. 36), c_s^2 = 1/3
+    double sw15;          // (3/2) sigma W  (Eq. 34)
+    double inv_W2;
+    double g[3];          // buoyancy per unit phi
+    double f_scale, inv_f_scale;
+};
+
+// Pointers of one state buffer: population planes in the storage type, plus the FP32
+// rest-population planes used by 16-bit storage.
+struct StateView {
+    void* f;      // 19 planes (flow only)
+    void* g;      // Q planes
+    void* hA;
+    void* hB;
+    float* rest;  // 3 planes (g_0, hA_0, hB_0) for 16-bit storage, else nullptr
+};
+
+enum { LAT_D2Q5 = 0, LAT_D3Q7 = 1 };
+
+// ------------------------------------------------------------------------------------
+// Velocity sets. Scalar sets: k = 0 at rest, then +x, -x, +y, -y (, +z, -z).
+// Flow set: D3Q19 in the order of the paper's table (§3). For every set the opposite of
+// k > 0 is k + 1 for odd k and k - 1 for even k.
+template <int LAT> struct Scalar;
+
+template <> struct Scalar<LAT_D2Q5> {
+    static constexpr int Q = 5;
+    __host__ __device__ static constexpr int ex(int k) { return k == 1 ? 1 : (k == 2 ? -1 : 0); }
+    __host__ __device__ static constexpr int ey(int k) { return k == 3 ? 1 : (k == 4 ? -1 : 0); }
+    __host__ __device__ static constexpr int ez(int) { return 0; }
+    __host__ __device__ static constexpr double w(int k) { return k == 0 ? 1.0 / 3.0 : 1.0 / 6.0; }
+    __host__ __device__ static constexpr double cs2() { return 1.0 / 3.0; }
+};
+
+template <> struct Scalar<LAT_D3Q7> {
+    static constexpr int Q = 7;
+    __host__ __device__ static constexpr int ex(int k) { return k == 1 ? 1 : (k == 2 ? -1 : 0); }
+    __host__ __device__ static constexpr int ey(int k) { return k == 3 ? 1 : (k == 4 ? -1 : 0); }
+    __host__ __device__ static constexpr int ez(int k) { return k == 5 ? 1 : (k == 6 ? -1 : 0); }
+    __host__ __device__ static constexpr double w(int k) { return k == 0 ? 0.25 : 0.125; }
+    __host__ __device__ static constexpr double cs2() { return 0.25; }
+};
+
+struct D3Q19 {
+    static constexpr int Q = 19;
+    __host__ __device__ static constexpr int ex(int k) {
+        return (k == 1 || k == 7 || k == 9 || k == 13 || k == 15) ? 1
+             : (k == 2 || k == 8 || k == 10 || k == 14 || k == 16) ? -1 : 0;
+    }
+    __host__ __device__ static constexpr int ey(int k) {
+        return (k == 3 || k == 7 || k == 11 || k == 14 || k == 17) ? 1
+             : (k == 4 || k == 8 || k == 12 || k == 13 || k == 18) ? -1 : 0;
+    }
+    __host__ __device__ static constexpr int ez(int k) {
+        return (k == 5 || k == 9 || k == 11 || k == 16 || k == 18) ? 1
+             : (k == 6 || k == 10 || k == 12 || k == 15 || k == 17) ? -1 : 0;
+    }
+    __host__ __device__ static constexpr double w(int k) {
+        return k == 0 ? 1.0 / 3.0 : (k <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+    }
+};
+
+__host__ __device__ constexpr int opp(int k) { return k == 0 ? 0 : ((k & 1) ? k + 1 : k - 1); }
+
+// ------------------------------------------------------------------------------------
+// Storage codecs. Real is the arithmetic type (double for FP64 storage, float otherwise).
+template <class T> struct RealOf { using type = float; };
+template <> struct RealOf<double> { using type = double; };
+
+// Which population set a plane belongs to, for the 16-bit deviation encoding.
+enum { SET_F = 0, SET_G = 1, SET_H = 2 };
+constexpr float kHScale = 64.0f;
+
+template <class T> struct Codec {
+    // plain FP32 / FP64 storage
+    template <int SET>
+    __device__ static typename RealOf<T>::type load(const T* p, double, const DevParams&) { return *p; }
+    template <int SET>
+    __device__ static void store(T* p, typename RealOf<T>::type v, double, const DevParams&) { *p = v; }
+};
+
+__device__ inline float to_f(__half v) { return __half2float(v); }
+__device__ inline float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <class T> __device__ inline T from_f(float v);
+template <> __device__ inline __half from_f<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ inline __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+template <class H> struct Codec16 {
+    // q = P / w - ref, scaled: f (ref 0, x f_scale), g (ref 1/2), h (ref 0, x 64)
+    template <int SET>
+    __device__ static float load(const H* p, double w, const DevParams& P) {
+        float q = to_f(*p);
+        if (SET == SET_F) return float(w) * (q * float(P.inv_f_scale));
+        if (SET == SET_G) return float(w) * (q + 0.5f);
+        return float(w) * (q * (1.0f / kHScale));
+    }
+    template <int SET>
+    __device__ static void store(H* p, float v, double w, const DevParams& P) {
+        float q = v * float(1.0 / w);
+        if (SET == SET_F) q *= float(P.f_scale);
+        else if (SET == SET_G) q -= 0.5f;
+        else q *= kHScale;
+        *p = from_f<H>(q);
+    }
+};
+template <> struct Codec<__half> : Codec16<__half> {};
+template <> struct Codec<__nv_bfloat16> : Codec16<__nv_bfloat16> {};
+
+template <class T> constexpr bool is16() { return sizeof(T) == 2; }
+
+// ------------------------------------------------------------------------------------
+// Pointwise model of §2 (Real precision).
+template <class R> __device__ __forceinline__ R interp_p(R f) { return f * f * (R(3) - R(2) * f); }
+template <class R> __device__ __forceinline__ R interp_dp(R f) { return R(6) * f * (R(1) - f); }
+template <class R> __device__ __forceinline__ R dwell_d(R f) { return R(16) * f * (R(1) - f) * (R(1) - R(2) * f); }
+
+// Eq. 33 written as mu = c - c_0^eq - p(phi) (c_1^eq - c_0^eq), since p(1 - phi) = 1 - p(phi)
+template <class R> __device__ __forceinline__ R closure(R c, R p, int a, const DevParams& P) {
+    return c - R(P.c0[a]) - p * R(P.dc[a]);
+}
+// Eq. 35 with Delta omega of Eq. 20 = sum mu (c_1^eq - c_0^eq)
+template <class R> __device__ __forceinline__ R source(R phi, R muA, R muB, const DevParams& P) {
+    if (P.source_off) return R(0);
+    R dom = muA * R(P.dc[0]) + muB * R(P.dc[1]);
+    return R(P.kphi) * (-dwell_d(phi) + R(P.lam) * interp_dp(phi) * dom);
+}
+
+// ------------------------------------------------------------------------------------
+// Addressing. Node index of (x, y, z) with x fastest.
+__device__ __forceinline__ long long node_of(int x, int y, int z, const DevParams& P) {
+    return ((long long)z * P.ny + y) * P.nx + x;
+}
+// Shift one coordinate by d; false when the result lies beyond a wall (no wrap there).
+__device__ __forceinline__ bool shift1(int& c, int d, int n, int wall) {
+    c += d;
+    if (c < 0) { if (wall) return false; c += n; }
+    else if (c >= n) { if (wall) return false; c -= n; }
+    return true;
+}
+__device__ __forceinline__ bool neighbour(int x, int y, int z, int dx, int dy, int dz,
+                                          const DevParams& P, long long& out) {
+    bool ok = shift1(x, dx, P.nx, P.wall_x);
+    ok = shift1(y, dy, P.ny, 0) && ok;
+    ok = shift1(z, dz, P.nz, P.wall_z) && ok;
+    out = node_of(x, y, z, P);
+    return ok;
+}
+
+// AA pattern. Even step: population k of node x is read from slot k of x and its
+// post-collision value written to slot opp(k) of x. Odd step: incoming k is read from
+// slot opp(k) of x - e_k and the post-collision value written to slot k of x + e_k;
+// across a wall both fall back to node x with the slots exchanged (half-way bounce-back).
+struct Slot { long long node; int slot; };
+
+__device__ __forceinline__ Slot read_slot(bool odd, int k, int ex, int ey, int ez,
+                                          int x, int y, int z, long long self, const DevParams& P) {
+    if (!odd || k == 0) return {self, k};
+    long long nb;
+    if (neighbour(x, y, z, -ex, -ey, -ez, P, nb)) return {nb, opp(k)};
+    return {self, k};
+}
+__device__ __forceinline__ Slot write_slot(bool odd, int k, int ex, int ey, int ez,
+                                           int x, int y, int z, long long self, const DevParams& P) {
+    if (k == 0) return {self, 0};
+    if (!odd) return {self, opp(k)};
+    long long nb;
+    if (neighbour(x, y, z, ex, ey, ez, P, nb)) return {nb, k};
+    return {self, opp(k)};
+}
+
+// Load / store one population of a scalar set, with the 16-bit rest planes in FP32.
+template <class T, int SET, int LAT>
+__device__ __forceinline__ typename RealOf<T>::type
+load_scalar(const T* base, const float* rest, int k, Slot s, const DevParams& P) {
+    if (is16<T>() && k == 0) return rest[s.node];
+    return Codec<T>::template load<SET>(base + (long long)s.slot * P.plane + s.node, Scalar<LAT>::w(k), P);
+}
+template <class T, int SET, int LAT>
+__device__ __forceinline__ void
+store_scalar(T* base, float* rest, int k, Slot s, typename RealOf<T>::type v, const DevParams& P) {
+    if (is16<T>() && k == 0) { rest[s.node] = float(v); return; }
+    Codec<T>::template store<SET>(base + (long long)s.slot * P.plane + s.node, v, Scalar<LAT>::w(k), P);
+}
+
+}  // namespace lbm

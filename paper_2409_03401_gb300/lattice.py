@@ -1,0 +1,121 @@
+"""Python front end of the C-ABI: PyTorch owns the device memory and the stream.
+
+``Simulation`` allocates the state and scratch buffers as torch tensors on a CUDA
+device, binds them with lbm_init, and forwards lbm_step / lbm_fields / lbm_reduce.
+Every step of the method runs in the sm_103a kernels of liblbm_gb300.so.
+"""
+import ctypes
+
+import torch
+
+from . import _lib
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Simulation:
+    """One lattice bound to caller-owned device memory.
+
+    ``params``: workloads.LBMParams. ``phi0, cA0, cB0``: float64 tensors of shape
+    (nz, ny, nx) on the target CUDA device (or on the host: they are copied).
+    """
+
+    def __init__(self, params, phi0, cA0, cB0, device=None, stream=None):
+        if device is None:
+            device = torch.device("cuda", torch.cuda.current_device())
+        device = torch.device(device)
+        if device.type != "cuda":
+            raise ValueError("Simulation needs a CUDA device")
+        self.lib = _lib.load()
+        self.params = params
+        self.device = device
+        self.stream = stream or torch.cuda.current_stream(device)
+        self._cp = _lib.make_params(params)
+        nbytes = self.lib.lbm_state_bytes(ctypes.byref(self._cp))
+        wbytes = self.lib.lbm_work_bytes(ctypes.byref(self._cp))
+        if nbytes == 0 or wbytes == 0:
+            raise _lib.LBMError(_lib.LBM_ERR_ARG, "invalid parameters")
+        # torch's caching allocator returns 512-byte aligned blocks
+        self.state = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.work = torch.empty(wbytes, dtype=torch.uint8, device=device)
+        self._ctx = ctypes.c_void_p()
+        self._init_fields = [t.to(device=device, dtype=torch.float64).contiguous() for t in (phi0, cA0, cB0)]
+        with torch.cuda.device(device):
+            _lib.check(self.lib.lbm_init(ctypes.byref(self._cp), _ptr(self.state), _ptr(self.work),
+                                              *[_ptr(t) for t in self._init_fields],
+                                              ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self._ctx)))
+
+    @classmethod
+    def attach(cls, params, state, t, device=None, stream=None):
+        """Resume from a state tensor saved earlier (checkpoint/resume)."""
+        self = cls.__new__(cls)
+        device = torch.device(device or state.device)
+        self.lib = _lib.load()
+        self.params = params
+        self.device = device
+        self.stream = stream or torch.cuda.current_stream(device)
+        self._cp = _lib.make_params(params)
+        wbytes = self.lib.lbm_work_bytes(ctypes.byref(self._cp))
+        self.state = state
+        self.work = torch.empty(wbytes, dtype=torch.uint8, device=device)
+        self._ctx = ctypes.c_void_p()
+        self._init_fields = []
+        _lib.check(self.lib.lbm_attach(ctypes.byref(self._cp), _ptr(self.state), _ptr(self.work), int(t),
+                                       ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self._ctx)))
+        return self
+
+    @property
+    def t(self):
+        return int(self.lib.lbm_time(self._ctx))
+
+    @property
+    def real_dtype(self):
+        return torch.float64 if self.params.storage == "f64" else torch.float32
+
+    def step(self, n=1):
+        _lib.check(self.lib.lbm_step(self._ctx, int(n)), self._ctx)
+        return self
+
+    def fields(self, names=_lib.FIELDS):
+        """Dict of (nz, ny, nx) tensors of the current time level."""
+        out = {k: torch.empty(self.params.shape, dtype=self.real_dtype, device=self.device) for k in names}
+        ptrs = (ctypes.c_void_p * _lib.NFIELDS)()
+        for i, k in enumerate(_lib.FIELDS):
+            ptrs[i] = out[k].data_ptr() if k in out else None
+        _lib.check(self.lib.lbm_fields(self._ctx, ptrs), self._ctx)
+        return out
+
+    def sums(self, raise_unstable=True):
+        """FP64 diagnostics (synchronises the stream)."""
+        buf = (ctypes.c_double * _lib.NRED)()
+        st = self.lib.lbm_reduce(self._ctx, buf)
+        if st != _lib.LBM_OK and (raise_unstable or st != _lib.LBM_ERR_UNSTABLE):
+            _lib.check(st, self._ctx)
+        return {k: buf[i] for i, k in enumerate(_lib.REDUCTIONS)}
+
+    def profile_begin(self, max_steps):
+        """Record CUDA events around this context's kernels for the next max_steps steps."""
+        _lib.check(self.lib.lbm_profile_begin(self._ctx, int(max_steps)), self._ctx)
+
+    def profile_end(self):
+        """(ms of phi passes, ms of fused step kernels, steps timed); synchronises."""
+        buf = (ctypes.c_double * 3)()
+        _lib.check(self.lib.lbm_profile_end(self._ctx, buf), self._ctx)
+        return buf[0], buf[1], int(buf[2])
+
+    @property
+    def kernels_per_step(self):
+        return int(self.lib.lbm_kernels_per_step(self._ctx))
+
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            self.lib.lbm_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,142 @@
+"""CUDA path vs the FP64 oracle, element by element, on seeded synthetic inputs.
+
+Tolerances (relative L-infinity, floors in tests/parity.py): FP64 storage 1e-12,
+FP32 storage 1e-5, FP16 storage 1e-3; BF16 storage (8-bit mantissa) is held to 1e-2
+and its measured gap is reported. Sizes span several thread blocks in x with a
+ragged tail (nx not a multiple of 128 or 32), both AA parities, walls and periodic
+wrap, and the degenerate one-node-thick directions.
+"""
+import pytest
+import torch
+
+from parity import TOL, compare, rel_linf, run_gpu, run_oracle
+from workloads import configs
+from workloads.params import LBMParams
+
+pytestmark = pytest.mark.gpu
+
+
+def _close(errs, tol):
+    bad = {k: v for k, v in errs.items() if not v <= tol}
+    assert not bad, f"tolerance {tol}: {bad} (all: {errs})"
+
+
+def test_diffusion_couple_fp64_full_size():
+    # the 2D couple at its full 512 x 8 size and full 4000-step length, FP64 storage
+    p, fields = configs.diffusion_couple()
+    _close(compare(p, fields(), 4000), TOL["f64"])
+
+
+@pytest.mark.parametrize("steps", [1, 2, 37])
+def test_ripening_fp32(steps):
+    p, fields = configs.ripening(shape=(20, 26, 150))     # 150 = 128 + ragged 22
+    _close(compare(p, fields(), steps), TOL["f32"])
+
+
+def test_ripening_fp32_long():
+    p, fields = configs.ripening(shape=(24, 24, 40))
+    _close(compare(p, fields(), 400), TOL["f32"])
+
+
+@pytest.mark.parametrize("steps", [1, 2, 25])
+def test_sedimentation_flow_fp32(steps):
+    p, fields = configs.sedimentation(shape=(18, 20, 140), fraction=0.05, r=(3.0, 5.0))
+    _close(compare(p, fields(), steps), TOL["f32"])
+
+
+def test_sedimentation_flow_fp32_long():
+    p, fields = configs.sedimentation(shape=(24, 22, 26), fraction=0.06, r=(3.0, 5.0))
+    _close(compare(p, fields(), 200), TOL["f32"])
+
+
+def test_flow_fp64_tight():
+    # same flow kernel in FP64 storage: agreement to round-off pins every term of the step
+    p, fields = configs.sedimentation(shape=(12, 14, 40), fraction=0.05, r=(3.0, 4.0), storage="f64")
+    _close(compare(p, fields(), 30), TOL["f64"])
+
+
+def test_ripening_fp64_tight():
+    p, fields = configs.ripening(shape=(12, 14, 33), storage="f64")
+    _close(compare(p, fields(), 50), TOL["f64"])
+
+
+def test_d2q5_fp32_and_walls():
+    p, fields = configs.diffusion_couple(nx=300, ny=5, storage="f32")
+    _close(compare(p, fields(), 300), TOL["f32"])
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_flow_16bit_storage(storage):
+    p, fields = configs.sedimentation(shape=(18, 20, 40), fraction=0.05, r=(3.0, 5.0), storage=storage)
+    errs = compare(p, fields(), 50)
+    print(f"{storage} storage errors after 50 steps: {errs}")
+    _close(errs, TOL[storage])
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_ripening_16bit_storage(storage):
+    p, fields = configs.ripening(shape=(16, 18, 40), storage=storage)
+    errs = compare(p, fields(), 100)
+    print(f"{storage} storage errors after 100 steps: {errs}")
+    _close(errs, TOL[storage])
+
+
+@pytest.mark.parametrize("shape,flow,walls", [
+    ((1, 1, 1), False, False), ((1, 1, 5), False, False), ((2, 1, 3), True, True),
+    ((3, 2, 1), True, False), ((1, 7, 1), True, False), ((4, 3, 2), True, True)])
+def test_degenerate_extents(shape, flow, walls):
+    # one-node-thick and one-node lattices: periodic self-neighbours and walls two planes apart
+    p = LBMParams(nx=shape[2], ny=shape[1], nz=shape[0], lattice="D3Q7", flow=flow, wall_z=walls)
+    g = torch.Generator().manual_seed(7)
+    phi = torch.rand(p.shape, generator=g, dtype=torch.float64)
+    cA = 0.3 + 0.1 * torch.rand(p.shape, generator=g, dtype=torch.float64)
+    cB = 0.3 + 0.1 * torch.rand(p.shape, generator=g, dtype=torch.float64)
+    _close(compare(p, (phi, cA, cB), 5), TOL["f32"])
+
+
+def test_adjoint_workload_forward_fp32():
+    p, fields = configs.adjoint_problem(shape=(20, 22, 24))
+    _close(compare(p, fields(), 120), TOL["f32"])
+
+
+def test_gpu_conservation_and_budget():
+    p, fields = configs.sedimentation(shape=(32, 30, 36), fraction=0.06, r=(3.0, 5.0))
+    from paper_2409_03401_gb300 import Simulation
+    sim = Simulation(p, *fields())
+    s0 = sim.sums()
+    o, _ = run_oracle(p, fields(), 0)
+    r0 = o.sums()
+    for k in ("phi", "cA", "cB", "g"):
+        assert abs(s0[k] - r0[k]) <= 1e-6 * abs(r0[k]), k
+    for _ in range(5):
+        sim.step(1)
+        s1 = sim.sums()
+        for k in ("cA", "cB"):
+            assert abs(s1[k] - s0[k]) <= 2e-6 * abs(s0[k]), k          # FP32 storage rounding only
+        assert abs(s1["g"] - (s0["g"] + s0["S"])) <= 2e-6 * abs(s0["g"])
+        assert s1["nonfinite"] == 0
+        s0 = s1
+
+
+def test_invalid_parameters_are_rejected():
+    from paper_2409_03401_gb300 import Simulation, LBMError
+    p, fields = configs.ripening(shape=(16, 16, 16))
+    with pytest.raises(LBMError):
+        Simulation(p.with_(M_phi=-0.3), *fields())
+    with pytest.raises(LBMError):
+        Simulation(p.with_(M=((-0.24, -0.24), (0.1, 0.1))), *fields())
+
+
+def test_unstable_run_is_reported():
+    # M_phi = 1.5 with W = 3: the source relaxes phi at the bulk values with rate
+    # 16 M_phi / W^2 = 2.7 per step > 2, so the explicit update diverges; the FP64
+    # reduction turns that into LBM_ERR_UNSTABLE instead of silently returning inf
+    from paper_2409_03401_gb300 import Simulation, LBMError
+    from paper_2409_03401_gb300._lib import LBM_ERR_UNSTABLE
+    p, fields = configs.ripening(shape=(16, 16, 16))
+    sim = Simulation(p.with_(M_phi=1.5), *fields())
+    sim.step(400)
+    with pytest.raises(LBMError) as e:
+        sim.sums()
+    assert e.value.status == LBM_ERR_UNSTABLE
+    assert sim.sums(raise_unstable=False)["nonfinite"] > 0

@@ -53,9 +53,9 @@ def _droplet_workload(p, fraction, r_min, r_max, seed):
             cache["g"] = place_droplets(p.shape, fraction, r_min, r_max, p.W, seed, walls=walls)
         return cache["g"]
 
-    def fields(device="cpu"):
+    def fields(device="cpu", z_range=None):
         centres, radii = geometry()
-        phi = phi_field(p.shape, centres, radii, p.W, walls=walls, device=device)
+        phi = phi_field(p.shape, centres, radii, p.W, walls=walls, device=device, z_range=z_range)
         cA, cB = composition_fields(phi, p.c_eq, SUPERSATURATION)
         return phi, cA, cB
     fields.geometry = geometry

@@ -31,15 +31,24 @@ def place_droplets(shape, fraction, r_min, r_max, W, seed, walls=(False, False, 
     """Return (centres [N, 3] as (x, y, z), radii [N]) as float64 numpy arrays.
 
     ``shape`` is (nz, ny, nx); ``walls`` flags the (x, y, z) axes bounded by
-    walls. For nz == 1 the droplets are discs in the z = 0 plane.
+    walls. For nz == 1 the droplets are discs in the z = 0 plane. Previous
+    droplets are looked up in a grid of cells no smaller than the largest
+    exclusion distance, which gives the same accept/reject sequence as testing
+    every previous droplet.
     """
     nz, ny, nx = shape
     ext = np.array([nx, ny, nz], dtype=np.float64)
     two_d = nz == 1
+    dims = 2 if two_d else 3
     box = nx * ny * (1 if two_d else nz)
     rng = SplitMix64(seed)
-    centres = np.zeros((0, 3))
-    radii = np.zeros((0,))
+    reach = 2.0 * r_max + W                                  # largest r_i + r_j + W
+    ncell = [max(1, int(ext[ax] // reach)) for ax in range(3)]
+    if two_d:
+        ncell[2] = 1
+    csize = [ext[ax] / ncell[ax] for ax in range(3)]
+    cells = {}
+    centres, radii = [], []
     covered = 0.0
     attempts = 0
     while covered < fraction * box:
@@ -48,29 +57,50 @@ def place_droplets(shape, fraction, r_min, r_max, W, seed, walls=(False, False, 
             raise RuntimeError(
                 f"droplet placement gave up after {max_attempts} attempts at fraction "
                 f"{covered / box:.4f} < {fraction}")
-        c = np.array([rng.uniform() * nx, rng.uniform() * ny, 0.0 if two_d else rng.uniform() * nz])
+        c = (rng.uniform() * nx, rng.uniform() * ny, 0.0 if two_d else rng.uniform() * nz)
         r = rng.uniform_range(r_min, r_max)
         ok = True
-        for ax in range(2 if two_d else 3):
+        for ax in range(dims):
             if walls[ax]:
-                lo = (c[ax] + 0.5) - r
-                hi = (ext[ax] - 0.5 - c[ax]) - r
-                if lo < W / 2 or hi < W / 2:
+                if (c[ax] + 0.5) - r < W / 2 or (ext[ax] - 0.5 - c[ax]) - r < W / 2:
                     ok = False
         if not ok:
             continue
-        if len(radii):
-            d = centres - c
-            for ax in range(3):
-                if not walls[ax] and not (two_d and ax == 2):
-                    d[:, ax] -= ext[ax] * np.round(d[:, ax] / ext[ax])
-            dist = np.sqrt((d * d).sum(axis=1))
-            if np.any(dist < radii + r + W):
-                continue
-        centres = np.vstack([centres, c[None]])
-        radii = np.append(radii, r)
+        home = [min(int(c[ax] / csize[ax]), ncell[ax] - 1) for ax in range(3)]
+        rng_ax = []
+        for ax in range(3):
+            if ncell[ax] == 1:
+                rng_ax.append((0,))
+            elif walls[ax] or (two_d and ax == 2):
+                rng_ax.append(tuple(i for i in (home[ax] - 1, home[ax], home[ax] + 1) if 0 <= i < ncell[ax]))
+            else:
+                rng_ax.append(tuple(sorted({(home[ax] + d) % ncell[ax] for d in (-1, 0, 1)})))
+        for ix in rng_ax[0]:
+            for iy in rng_ax[1]:
+                for iz in rng_ax[2]:
+                    for j in cells.get((ix, iy, iz), ()):
+                        d2 = 0.0
+                        for ax in range(dims):
+                            d = centres[j][ax] - c[ax]
+                            if not walls[ax]:
+                                d -= ext[ax] * round(d / ext[ax])
+                            d2 += d * d
+                        if d2 < (radii[j] + r + W) ** 2:
+                            ok = False
+                            break
+                    if not ok:
+                        break
+                if not ok:
+                    break
+            if not ok:
+                break
+        if not ok:
+            continue
+        cells.setdefault(tuple(home), []).append(len(radii))
+        centres.append(c)
+        radii.append(r)
         covered += math.pi * r * r if two_d else 4.0 / 3.0 * math.pi * r ** 3
-    return centres, radii
+    return np.array(centres, dtype=np.float64).reshape(-1, 3), np.array(radii, dtype=np.float64)
 
 
 def _axis_points(c, R, n, periodic, device):
@@ -92,10 +122,14 @@ def _axis_points(c, R, n, periodic, device):
 
 
 def phi_field(shape, centres, radii, W, walls=(False, False, False), device="cpu",
-              dtype=torch.float64, cutoff_widths=5.0):
-    """Droplet phase field of shape (nz, ny, nx) (see the module docstring)."""
+              dtype=torch.float64, cutoff_widths=5.0, z_range=None):
+    """Droplet phase field of shape (nz, ny, nx) (see the module docstring).
+
+    ``z_range=(z0, z1)`` returns only the planes z0 <= z < z1 of that field.
+    """
     nz, ny, nx = shape
-    phi = torch.zeros(shape, dtype=torch.float64, device=device)
+    z0, z1 = z_range if z_range is not None else (0, nz)
+    phi = torch.zeros((z1 - z0, ny, nx), dtype=torch.float64, device=device)
     for (cx, cy, cz), r in zip(np.asarray(centres), np.asarray(radii)):
         R = float(r) + cutoff_widths * W
         ix, dx = _axis_points(float(cx), R, nx, not walls[0], device)
@@ -105,6 +139,10 @@ def phi_field(shape, centres, radii, W, walls=(False, False, False), device="cpu
             dz = torch.zeros(1, dtype=torch.float64, device=device)
         else:
             iz, dz = _axis_points(float(cz), R, nz, not walls[2], device)
+        keep = (iz >= z0) & (iz < z1)
+        if not bool(keep.any()):
+            continue
+        iz, dz = iz[keep] - z0, dz[keep]
         dist = torch.sqrt(dz[:, None, None] ** 2 + dy[None, :, None] ** 2 + dx[None, None, :] ** 2)
         prof = 0.5 * (1.0 + torch.tanh(2.0 * (float(r) - dist) / W))
         sel = (iz[:, None, None], iy[None, :, None], ix[None, None, :])
