@@ -25,7 +25,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "coupled-step MLUPS at 512^3 + % HBM roofline; FP16-store and adjoint vs FP32"
 N = 512
-ALG_BYTES_PER_NODE = {"f32": 320.0, "f16": 168.0, "bf16": 168.0, "f64": 640.0}
+# bytes each node reads and writes per step: 40 populations; 16-bit storage keeps the
+# four rest populations g_0, h^A_0, h^B_0, f_0 in FP32 (36 x 2 B + 4 x 4 B = 88 B each way)
+ALG_BYTES_PER_NODE = {"f32": 320.0, "f16": 176.0, "bf16": 176.0, "f64": 640.0}
 
 
 def parse():
@@ -167,6 +169,41 @@ def time_device(sim, steps, warmup, dist):
     return ms, ms_phi / max(nprof, 1), ms_step / max(nprof, 1)
 
 
+def time_adjoint(device, n=128, steps=200, K=100):
+    """Cost of the hand-written adjoint on the 128^3 ripening workload (FP32, no flow):
+    forward ms/step vs backward ms/step (recompute from checkpoints + adjoint sweep)."""
+    import torch
+    from workloads import configs
+    from paper_2409_03401_gb300.adjoint import CoupledRun, forward_fields, misfit
+    p, fields = configs.adjoint_problem(n=n)
+    phi0, cA0, cB0 = fields(device=device)
+    target = forward_fields(p, configs.THETA_TARGET, phi0, cA0, cB0, steps, device=device)
+    forward_fields(p, configs.THETA_EVAL, phi0, cA0, cB0, 10, device=device)   # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    forward_fields(p, configs.THETA_EVAL, phi0, cA0, cB0, steps, device=device)
+    torch.cuda.synchronize()
+    fwd = time.perf_counter() - t0
+    th = torch.tensor(configs.THETA_EVAL, dtype=torch.float64, requires_grad=True)
+    p0 = phi0.clone().requires_grad_(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = CoupledRun.apply(p0, th, p, cA0, cB0, steps, K)
+    L = misfit(out, target)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    L.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    return {"workload": f"{n}^3 ripening, FP32, {steps} steps, checkpoint every {K}",
+            "forward_ms_per_step": fwd / steps * 1e3,
+            "checkpointed_forward_ms_per_step": (t1 - t0) / steps * 1e3,
+            "backward_ms_per_step": (t2 - t1) / steps * 1e3,
+            "backward_over_forward": (t2 - t1) / fwd,
+            "alg_bytes_per_node": {"forward": 168, "recompute": 168, "adjoint_step": 252},
+            "grad_theta": [float(v) for v in th.grad]}
+
+
 def run_e2e(p, init, steps, device):
     """Same metric through the public API with host buffers: pinned host inputs copied
     in, init, K steps, phi and mu copied out, FP64 sums read back, all in the timed region."""
@@ -252,6 +289,9 @@ def gb300(args):
             del v
             torch.cuda.synchronize()
         out["variants"] = var
+
+    if not args.no_variants:
+        out["variants"]["adjoint"] = time_adjoint(device)
 
     if not args.no_e2e:
         out["e2e"] = run_e2e(p, init, args.steps, device)

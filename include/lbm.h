@@ -9,7 +9,8 @@
  *   f     - incompressible flow with capillary + buoyancy forcing  (§3.1, Eqs. 36-45, 34)
  * g, h^A, h^B use D2Q5 (2D) or D3Q7 (3D); f uses the D3Q19 set of the paper's table.
  * One call of lbm_step advances every population set by one fused collide-and-stream
- * pass over HBM with in-place AA-pattern streaming.
+ * pass over HBM: in-place AA-pattern streaming without flow; with flow, by default, a
+ * two-buffer pull step that computes the capillary stencil's phi on the fly.
  *
  * Memory: every device buffer is allocated and owned by the caller (for instance a
  * torch tensor); the library never allocates or frees device memory. The context is
@@ -42,7 +43,12 @@ typedef enum { LBM_D2Q5 = 0, LBM_D3Q7 = 1 } lbm_lattice;
 /* Storage type of the populations. Arithmetic is FP64 for LBM_F64 and FP32 otherwise.
  * LBM_F16 / LBM_BF16 store every moving population as a 16-bit deviation from its
  * lattice-weight reference, q_k = P_k / w_k - ref (f: ref 0 times f_scale; g: ref 1/2;
- * h: ref 0 times 64); the three rest populations g_0, h^A_0, h^B_0 stay FP32. */
+ * h: ref 0 times 64); the rest populations g_0, h^A_0, h^B_0, f_0 stay FP32 and receive the
+ * rounding residual of the node's moving populations at every store, so the node's sums
+ * (phi, c^A, c^B, p_h) are carried to FP32 accuracy.
+ * In every storage type the rest populations h^alpha_0 are kept shifted by the constant
+ * c_0^{alpha,eq} (h_0 - c_0^eq), so that the sum of the h populations is c - c_0^eq and
+ * mu (Eq. 33) does not inherit the rounding of c itself. */
 typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16 = 2, LBM_BF16 = 3 } lbm_storage;
 
 /* Model parameters in lattice units (dx = dt = 1, rho_0 = 1), named as in the paper. */
@@ -54,7 +60,10 @@ typedef struct lbm_params {
     int32_t wall_x;          /* 1: half-way bounce-back planes at x = -1/2 and nx - 1/2 */
     int32_t wall_z;          /* 1: half-way bounce-back planes at z = -1/2 and nz - 1/2 */
     int32_t source_off;      /* 1: S_phi = 0 (pure advection-diffusion of phi; test switch) */
-    int32_t reserved;        /* must be 0 */
+    int32_t inplace;         /* flow only. 0: two state copies, one fused kernel per step (the
+                              * capillary stencil's phi is computed on the fly in shared memory);
+                              * 1: one in-place AA-pattern copy (half the memory) plus a phi pass.
+                              * Without flow the state is always one in-place AA-pattern copy. */
     double W;                /* interface width (Eq. 14) */
     double lambda;           /* coupling constant lambda = K / H (§2.2) */
     double M_phi;            /* scaled phase-field mobility, M_phi = W^2 / tau_phi */
@@ -138,8 +147,54 @@ lbm_status lbm_reduce(lbm_ctx* ctx, double* out);
 lbm_status lbm_profile_begin(lbm_ctx* ctx, int max_steps);
 lbm_status lbm_profile_end(lbm_ctx* ctx, double* out);
 
-/* Number of kernels one lbm_step(ctx, 1) launches (2 with flow, else 1). */
+/* Number of kernels one lbm_step(ctx, 1) launches (2 for in-place flow, else 1). */
 int lbm_kernels_per_step(const lbm_ctx* ctx);
+
+/* One step out of place, without a context: d_src holds one state copy at time t (the
+ * layout lbm_init writes: lbm_copy_bytes bytes), d_dst receives time t + 1 in the same
+ * layout; d_src is not modified. d_work as for lbm_init (used by in-place flow). The
+ * adjoint's recompute pass uses it to rebuild the states of a segment from a checkpoint. */
+lbm_status lbm_step_buffers(const lbm_params* p, const void* d_src, void* d_dst, int64_t t,
+                            void* d_work, void* stream);
+
+/* Bytes of one state copy (lbm_state_bytes is one or two copies). */
+size_t lbm_copy_bytes(const lbm_params* p);
+
+/* ---- Discrete adjoint of the coupled step without flow (storage LBM_F32 or LBM_F64) ----
+ * The method's reverse mode: with Lambda_t = dL/dP_t the adjoint of the incoming
+ * populations at time t (canonical layout: 3*Q planes ordered g, h^A, h^B, each plane
+ * population k, element = node, in the arithmetic type), one reverse step is
+ * Lambda_t = J_C(P_t)^T S^T Lambda_{t+1}, the transpose of the local BGK collision
+ * (Eqs. 20, 33, 35, 46-51) after the reverse of the streaming; the gradient with respect to
+ * the mobilities M[pi][alpha] and M_phi accumulates in FP64 in d_adj_work. Flow is not
+ * supported (LBM_ERR_STATE). Everything is asynchronous on ``stream`` except
+ * lbm_adjoint_theta. These calls allocate nothing. */
+size_t lbm_adjoint_bytes(const lbm_params* p);       /* one Lambda field */
+size_t lbm_adjoint_work_bytes(const lbm_params* p);  /* FP64 gradient partials */
+
+/* Zero the gradient partials. */
+lbm_status lbm_adjoint_reset(const lbm_params* p, void* d_adj_work, void* stream);
+
+/* Lambda_T from the adjoint of the fields at time T: d_phib, d_muAb, d_muBb hold
+ * dL/dphi, dL/dmu^A, dL/dmu^B per node (arithmetic type; NULL = zero); d_state is the state
+ * copy at time t (in-place layout). Adds the M_phi part of the seed to the partials. */
+lbm_status lbm_adjoint_seed(const lbm_params* p, const void* d_state, int64_t t, const void* d_phib,
+                            const void* d_muAb, const void* d_muBb, void* d_lam, void* d_adj_work,
+                            void* stream);
+
+/* Lambda_t (d_lam) from Lambda_{t+1} (d_lam_next) at the state copy of time t. */
+lbm_status lbm_adjoint_step(const lbm_params* p, const void* d_state, int64_t t, const void* d_lam_next,
+                            void* d_lam, void* d_adj_work, void* stream);
+
+/* dL/dphi_0 (FP64, per node) from Lambda_0 through the initial populations of lbm_init;
+ * adds the M_phi part of the initial source to the partials. */
+lbm_status lbm_adjoint_init(const lbm_params* p, const double* d_phi0, const double* d_cA0,
+                            const double* d_cB0, const void* d_lam0, double* d_phi0b, void* d_adj_work,
+                            void* stream);
+
+/* Sum the partials: out[0..4] = dL/dM[0][A], dL/dM[0][B], dL/dM[1][A], dL/dM[1][B], dL/dM_phi.
+ * Synchronises the stream. */
+lbm_status lbm_adjoint_theta(const lbm_params* p, void* d_adj_work, double* out, void* stream);
 
 /* Release the context (host memory only; device buffers remain the caller's). */
 lbm_status lbm_destroy(lbm_ctx* ctx);

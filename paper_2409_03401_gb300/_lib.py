@@ -25,7 +25,7 @@ class lbm_params(ctypes.Structure):
         ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
         ("lattice", ctypes.c_int32), ("flow", ctypes.c_int32), ("storage", ctypes.c_int32),
         ("wall_x", ctypes.c_int32), ("wall_z", ctypes.c_int32), ("source_off", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("inplace", ctypes.c_int32),
         ("W", ctypes.c_double), ("lambda_", ctypes.c_double), ("M_phi", ctypes.c_double),
         ("c_eq", (ctypes.c_double * 2) * 2), ("M", (ctypes.c_double * 2) * 2),
         ("nu", ctypes.c_double), ("sigma", ctypes.c_double), ("g", ctypes.c_double * 3),
@@ -67,6 +67,15 @@ def load():
         "lbm_profile_begin": (ctypes.c_int, [vp, ctypes.c_int]),
         "lbm_profile_end": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double)]),
         "lbm_kernels_per_step": (ctypes.c_int, [vp]),
+        "lbm_copy_bytes": (ctypes.c_size_t, [P]),
+        "lbm_step_buffers": (ctypes.c_int, [P, vp, vp, ctypes.c_int64, vp, vp]),
+        "lbm_adjoint_bytes": (ctypes.c_size_t, [P]),
+        "lbm_adjoint_work_bytes": (ctypes.c_size_t, [P]),
+        "lbm_adjoint_reset": (ctypes.c_int, [P, vp, vp]),
+        "lbm_adjoint_seed": (ctypes.c_int, [P, vp, ctypes.c_int64, vp, vp, vp, vp, vp, vp]),
+        "lbm_adjoint_step": (ctypes.c_int, [P, vp, ctypes.c_int64, vp, vp, vp, vp]),
+        "lbm_adjoint_init": (ctypes.c_int, [P, vp, vp, vp, vp, vp, vp, vp]),
+        "lbm_adjoint_theta": (ctypes.c_int, [P, vp, ctypes.POINTER(ctypes.c_double), vp]),
         "lbm_last_error": (ctypes.c_char_p, [vp]),
         "lbm_build_info": (ctypes.c_char_p, []),
     }
@@ -82,7 +91,9 @@ def exported_symbols():
     """Names of the C-ABI entry points this binding expects."""
     return ["lbm_state_bytes", "lbm_work_bytes", "lbm_init", "lbm_attach", "lbm_step", "lbm_time",
             "lbm_fields", "lbm_reduce", "lbm_profile_begin", "lbm_profile_end", "lbm_kernels_per_step",
-            "lbm_destroy", "lbm_last_error", "lbm_build_info"]
+            "lbm_copy_bytes", "lbm_step_buffers", "lbm_adjoint_bytes", "lbm_adjoint_work_bytes",
+            "lbm_adjoint_reset", "lbm_adjoint_seed", "lbm_adjoint_step", "lbm_adjoint_init",
+            "lbm_adjoint_theta", "lbm_destroy", "lbm_last_error", "lbm_build_info"]
 
 
 def check(status, ctx=None):
@@ -100,7 +111,7 @@ def make_params(p):
     c.storage = STORAGE[p.storage]
     c.wall_x, c.wall_z = int(p.wall_x), int(p.wall_z)
     c.source_off = int(p.source_off)
-    c.reserved = 0
+    c.inplace = int(getattr(p, "inplace", False))
     c.W, c.lambda_, c.M_phi = p.W, p.lam, p.M_phi
     for i in range(2):
         for a in range(2):

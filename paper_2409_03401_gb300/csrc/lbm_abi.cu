@@ -26,6 +26,8 @@ thread_local std::string g_last_error = "no error";
 
 struct Layout {
     long long n = 0, plane = 0;
+    bool two = false;          // two state copies (fused pull step with flow)
+    size_t copy = 0;           // bytes of one copy
     size_t state = 0, work = 0;
     size_t off_f = 0, off_g = 0, off_hA = 0, off_hB = 0, off_rest = 0;
     size_t off_phi = 0, off_partials = 0, off_out = 0;
@@ -35,12 +37,13 @@ const char* check_params(const lbm_params* p) {
     if (!p) return "params is NULL";
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) return "lattice extents must be >= 1";
     if (p->ny > 65535 || p->nz > 65535) return "ny and nz must be <= 65535";
+    if ((long long)p->nx * p->ny * p->nz >= (1LL << 31)) return "nx*ny*nz must be < 2^31";
     if (p->lattice != LBM_D2Q5 && p->lattice != LBM_D3Q7) return "lattice must be LBM_D2Q5 or LBM_D3Q7";
     if (p->lattice == LBM_D2Q5 && p->nz != 1) return "LBM_D2Q5 needs nz == 1";
     if (p->flow != 0 && p->flow != 1) return "flow must be 0 or 1";
     if (p->flow && p->lattice != LBM_D3Q7) return "flow needs the 3D lattice (LBM_D3Q7 scalars, D3Q19 flow)";
     if (p->storage < LBM_F64 || p->storage > LBM_BF16) return "storage must be one of lbm_storage";
-    if (p->reserved != 0) return "reserved must be 0";
+    if (p->inplace != 0 && p->inplace != 1) return "inplace must be 0 or 1";
     if (!(p->W > 0)) return "W must be > 0";
     if (!(p->M_phi > 0)) return "M_phi must be > 0";
     for (int ph = 0; ph < 2; ++ph)
@@ -63,8 +66,10 @@ Layout layout_of(const lbm_params* p) {
     L.off_g = o;  o += Q * pb;
     L.off_hA = o; o += Q * pb;
     L.off_hB = o; o += Q * pb;
-    L.off_rest = o; o += is16(p->storage) ? 3 * (size_t)L.plane * sizeof(float) : 0;
-    L.state = round_up(o, kAlign);
+    L.off_rest = o; o += is16(p->storage) ? 4 * (size_t)L.plane * sizeof(float) : 0;
+    L.copy = round_up(o, kAlign);
+    L.two = p->flow && !p->inplace;
+    L.state = L.copy * (L.two ? 2 : 1);
     const size_t real = p->storage == LBM_F64 ? 8 : 4;
     size_t w = 0;
     L.off_phi = w;      w += p->flow ? round_up((size_t)L.plane * real, kAlign) : 0;
@@ -106,7 +111,8 @@ struct lbm_ctx {
     lbm_params p;
     Layout L;
     DevParams dp;
-    StateView st;
+    StateView st;                  // copy 0 (the only copy for the in-place layout)
+    StateView st1;                 // copy 1 of the two-buffer layout
     char* work;
     cudaStream_t stream;
     int64_t t;
@@ -169,12 +175,16 @@ lbm_status bind(const lbm_params* p, void* d_state, void* d_work, void* stream, 
     c->p = *p;
     c->L = layout_of(p);
     c->dp = dev_params(p, c->L);
-    char* s = static_cast<char*>(d_state);
-    c->st.f = p->flow ? s + c->L.off_f : nullptr;
-    c->st.g = s + c->L.off_g;
-    c->st.hA = s + c->L.off_hA;
-    c->st.hB = s + c->L.off_hB;
-    c->st.rest = is16(p->storage) ? reinterpret_cast<float*>(s + c->L.off_rest) : nullptr;
+    for (int cp = 0; cp < (c->L.two ? 2 : 1); ++cp) {
+        char* s = static_cast<char*>(d_state) + cp * c->L.copy;
+        StateView& v = cp == 0 ? c->st : c->st1;
+        v.f = p->flow ? s + c->L.off_f : nullptr;
+        v.g = s + c->L.off_g;
+        v.hA = s + c->L.off_hA;
+        v.hB = s + c->L.off_hB;
+        v.rest = is16(p->storage) ? reinterpret_cast<float*>(s + c->L.off_rest) : nullptr;
+    }
+    if (!c->L.two) c->st1 = c->st;
     c->work = static_cast<char*>(d_work);
     c->stream = static_cast<cudaStream_t>(stream);
     c->t = 0;
@@ -182,6 +192,26 @@ lbm_status bind(const lbm_params* p, void* d_state, void* d_work, void* stream, 
     *out = c;
     return LBM_OK;
 }
+
+// Views of one state copy starting at base.
+StateView view_of(const lbm_params* p, const Layout& L, void* base) {
+    StateView v{};
+    char* s = static_cast<char*>(base);
+    v.f = p->flow ? s + L.off_f : nullptr;
+    v.g = s + L.off_g;
+    v.hA = s + L.off_hA;
+    v.hB = s + L.off_hB;
+    v.rest = is16(p->storage) ? reinterpret_cast<float*>(s + L.off_rest) : nullptr;
+    return v;
+}
+
+// State view holding time level t and the streaming mode that reads it.
+const StateView& current(const lbm_ctx* c) { return (c->L.two && (c->t & 1)) ? c->st1 : c->st; }
+int read_mode(const lbm_ctx* c) {
+    if (c->L.two) return lbm::kModePull;
+    return (c->t & 1) ? lbm::kModeAAOdd : lbm::kModeAAEven;
+}
+int zchunk_of(const lbm_ctx* c) { return c->p.nz < 64 ? c->p.nz : 64; }
 
 }  // namespace
 
@@ -207,8 +237,8 @@ lbm_status lbm_init(const lbm_params* p, void* d_state, void* d_work, const doub
     if (s != LBM_OK) return s;
     lbm_ctx* c = *out;
     cudaGetLastError();
-    LBM_DISPATCH(c->p.storage, launch_init, c->dp, c->st, c->p.lattice, c->p.flow != 0, d_phi0, d_cA0, d_cB0,
-                 c->stream);
+    LBM_DISPATCH(c->p.storage, launch_init, c->dp, c->st, c->p.lattice, c->p.flow != 0, c->L.two, d_phi0, d_cA0,
+                 d_cB0, c->stream);
     s = cuda_check(c, "init kernel launch");
     if (s != LBM_OK) {
         g_last_error = c->err;
@@ -233,17 +263,23 @@ lbm_status lbm_step(lbm_ctx* c, int nsteps) {
     if (nsteps < 0) return fail(c, LBM_ERR_ARG, "nsteps must be >= 0");
     cudaGetLastError();
     for (int i = 0; i < nsteps; ++i) {
-        const bool odd = (c->t & 1) != 0;
+        const int mode = read_mode(c);
         const bool timed = c->prof_n < c->prof_max;
         cudaEvent_t* e = timed ? &c->ev[3 * c->prof_n] : nullptr;
         if (timed) cudaEventRecord(e[0], c->stream);
-        if (c->p.flow) {
-            LBM_DISPATCH(c->p.storage, launch_phi, c->dp, c->st, c->p.lattice, odd, c->work + c->L.off_phi,
+        if (c->p.flow && !c->L.two) {
+            LBM_DISPATCH(c->p.storage, launch_phi, c->dp, c->st, c->p.lattice, mode, c->work + c->L.off_phi,
                          c->stream);
         }
         if (timed) cudaEventRecord(e[1], c->stream);
-        LBM_DISPATCH(c->p.storage, launch_step, c->dp, c->st, c->p.lattice, c->p.flow != 0, odd,
-                     c->work + c->L.off_phi, c->stream);
+        if (c->L.two) {
+            const StateView& src = current(c);
+            const StateView& dst = (c->t & 1) ? c->st : c->st1;
+            LBM_DISPATCH(c->p.storage, launch_fused, c->dp, src, dst, zchunk_of(c), c->stream);
+        } else {
+            LBM_DISPATCH(c->p.storage, launch_step, c->dp, c->st, c->st, c->p.lattice, c->p.flow != 0, mode,
+                         c->work + c->L.off_phi, c->stream);
+        }
         if (timed) { cudaEventRecord(e[2], c->stream); c->prof_n += 1; }
         c->t += 1;
     }
@@ -286,7 +322,7 @@ lbm_status lbm_profile_end(lbm_ctx* c, double* out) {
     return cuda_check(c, "profile events");
 }
 
-int lbm_kernels_per_step(const lbm_ctx* c) { return c ? (c->p.flow ? 2 : 1) : 0; }
+int lbm_kernels_per_step(const lbm_ctx* c) { return c ? ((c->p.flow && !c->L.two) ? 2 : 1) : 0; }
 
 int64_t lbm_time(const lbm_ctx* c) { return c ? c->t : -1; }
 
@@ -296,8 +332,7 @@ lbm_status lbm_fields(lbm_ctx* c, void* const* dst) {
     lbm::FieldPtrs fp;
     for (int i = 0; i < LBM_NFIELDS; ++i) fp.p[i] = dst[i];
     cudaGetLastError();
-    const bool odd = (c->t & 1) != 0;
-    LBM_DISPATCH(c->p.storage, launch_fields, c->dp, c->st, c->p.lattice, c->p.flow != 0, odd,
+    LBM_DISPATCH(c->p.storage, launch_fields, c->dp, current(c), c->p.lattice, c->p.flow != 0, read_mode(c),
                  c->work + c->L.off_phi, fp, c->stream);
     return cuda_check(c, "fields kernel launch");
 }
@@ -306,10 +341,9 @@ lbm_status lbm_reduce(lbm_ctx* c, double* out) {
     if (!c) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
     if (!out) return fail(c, LBM_ERR_ARG, "out is NULL");
     cudaGetLastError();
-    const bool odd = (c->t & 1) != 0;
     double* partials = reinterpret_cast<double*>(c->work + c->L.off_partials);
     double* dout = reinterpret_cast<double*>(c->work + c->L.off_out);
-    LBM_DISPATCH(c->p.storage, launch_reduce, c->dp, c->st, c->p.lattice, c->p.flow != 0, odd,
+    LBM_DISPATCH(c->p.storage, launch_reduce, c->dp, current(c), c->p.lattice, c->p.flow != 0, read_mode(c),
                  c->work + c->L.off_phi, partials, kRedBlocks, c->stream);
     reduce_final<<<1, 256, 0, c->stream>>>(partials, kRedBlocks, dout);
     lbm_status s = cuda_check(c, "reduce kernel launch");
@@ -319,6 +353,117 @@ lbm_status lbm_reduce(lbm_ctx* c, double* out) {
     if (e != cudaSuccess) return fail(c, LBM_ERR_CUDA, std::string("reduce copy: ") + cudaGetErrorString(e));
     if (out[LBM_RED_NONFINITE] != 0.0)
         return fail(c, LBM_ERR_UNSTABLE, "non-finite moments in the state (unstable run)");
+    return LBM_OK;
+}
+
+size_t lbm_copy_bytes(const lbm_params* p) {
+    if (check_params(p)) return 0;
+    return layout_of(p).copy;
+}
+
+lbm_status lbm_step_buffers(const lbm_params* p, const void* d_src, void* d_dst, int64_t t, void* d_work,
+                            void* stream) {
+    if (const char* m = check_params(p)) return fail(nullptr, LBM_ERR_ARG, m);
+    if (!d_src || !d_dst || t < 0) return fail(nullptr, LBM_ERR_ARG, "buffers must be non-NULL and t >= 0");
+    if (d_src == d_dst) return fail(nullptr, LBM_ERR_ARG, "d_src and d_dst must differ");
+    const Layout L = layout_of(p);
+    if (p->flow && p->inplace && !d_work) return fail(nullptr, LBM_ERR_ARG, "in-place flow needs d_work");
+    const DevParams dp = dev_params(p, L);
+    const StateView src = view_of(p, L, const_cast<void*>(d_src));
+    const StateView dst = view_of(p, L, d_dst);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaGetLastError();
+    if (L.two) {
+        const int zc = p->nz < 64 ? p->nz : 64;
+        LBM_DISPATCH(p->storage, launch_fused, dp, src, dst, zc, s);
+    } else {
+        const int mode = (t & 1) ? lbm::kModeAAOdd : lbm::kModeAAEven;
+        char* phi = static_cast<char*>(d_work) + L.off_phi;
+        if (p->flow) { LBM_DISPATCH(p->storage, launch_phi, dp, src, p->lattice, mode, phi, s); }
+        LBM_DISPATCH(p->storage, launch_step, dp, src, dst, p->lattice, p->flow != 0, mode, phi, s);
+    }
+    return cuda_check(nullptr, "step_buffers kernel launch");
+}
+
+namespace {
+const char* check_adjoint(const lbm_params* p) {
+    if (const char* m = check_params(p)) return m;
+    if (p->flow) return "the adjoint covers the step without flow";
+    if (p->storage != LBM_F32 && p->storage != LBM_F64) return "the adjoint needs LBM_F32 or LBM_F64 storage";
+    return nullptr;
+}
+size_t real_size(const lbm_params* p) { return p->storage == LBM_F64 ? 8 : 4; }
+}  // namespace
+
+size_t lbm_adjoint_bytes(const lbm_params* p) {
+    if (check_adjoint(p)) return 0;
+    return round_up(3 * (size_t)scalar_q(p->lattice) * layout_of(p).plane * real_size(p), kAlign);
+}
+
+size_t lbm_adjoint_work_bytes(const lbm_params* p) {
+    if (check_adjoint(p)) return 0;
+    return round_up((size_t)(lbm::adjoint_blocks() + 1) * lbm::adjoint_ntheta() * sizeof(double), kAlign);
+}
+
+lbm_status lbm_adjoint_reset(const lbm_params* p, void* d_adj_work, void* stream) {
+    if (const char* m = check_adjoint(p)) return fail(nullptr, check_params(p) ? LBM_ERR_ARG : LBM_ERR_STATE, m);
+    if (!d_adj_work) return fail(nullptr, LBM_ERR_ARG, "d_adj_work is NULL");
+    cudaError_t e = cudaMemsetAsync(d_adj_work, 0, lbm_adjoint_work_bytes(p), static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail(nullptr, LBM_ERR_CUDA, std::string("adjoint reset: ") + cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+lbm_status lbm_adjoint_seed(const lbm_params* p, const void* d_state, int64_t t, const void* d_phib,
+                            const void* d_muAb, const void* d_muBb, void* d_lam, void* d_adj_work, void* stream) {
+    if (const char* m = check_adjoint(p)) return fail(nullptr, check_params(p) ? LBM_ERR_ARG : LBM_ERR_STATE, m);
+    if (!d_state || !d_lam || !d_adj_work || t < 0) return fail(nullptr, LBM_ERR_ARG, "NULL buffer or t < 0");
+    const Layout L = layout_of(p);
+    cudaGetLastError();
+    lbm::launch_adjoint_seed(dev_params(p, L), view_of(p, L, const_cast<void*>(d_state)), p->storage, p->lattice,
+                             (t & 1) != 0, d_phib, d_muAb, d_muBb, d_lam, static_cast<double*>(d_adj_work),
+                             static_cast<cudaStream_t>(stream));
+    return cuda_check(nullptr, "adjoint seed launch");
+}
+
+lbm_status lbm_adjoint_step(const lbm_params* p, const void* d_state, int64_t t, const void* d_lam_next,
+                            void* d_lam, void* d_adj_work, void* stream) {
+    if (const char* m = check_adjoint(p)) return fail(nullptr, check_params(p) ? LBM_ERR_ARG : LBM_ERR_STATE, m);
+    if (!d_state || !d_lam || !d_lam_next || !d_adj_work || t < 0)
+        return fail(nullptr, LBM_ERR_ARG, "NULL buffer or t < 0");
+    if (d_lam == d_lam_next) return fail(nullptr, LBM_ERR_ARG, "d_lam and d_lam_next must differ");
+    const Layout L = layout_of(p);
+    cudaGetLastError();
+    lbm::launch_adjoint_step(dev_params(p, L), view_of(p, L, const_cast<void*>(d_state)), p->storage, p->lattice,
+                             (t & 1) != 0, d_lam_next, d_lam, static_cast<double*>(d_adj_work),
+                             static_cast<cudaStream_t>(stream));
+    return cuda_check(nullptr, "adjoint step launch");
+}
+
+lbm_status lbm_adjoint_init(const lbm_params* p, const double* d_phi0, const double* d_cA0, const double* d_cB0,
+                            const void* d_lam0, double* d_phi0b, void* d_adj_work, void* stream) {
+    if (const char* m = check_adjoint(p)) return fail(nullptr, check_params(p) ? LBM_ERR_ARG : LBM_ERR_STATE, m);
+    if (!d_phi0 || !d_cA0 || !d_cB0 || !d_lam0 || !d_phi0b || !d_adj_work)
+        return fail(nullptr, LBM_ERR_ARG, "NULL buffer");
+    const Layout L = layout_of(p);
+    cudaGetLastError();
+    lbm::launch_adjoint_init(dev_params(p, L), p->storage, p->lattice, d_phi0, d_cA0, d_cB0, d_lam0, d_phi0b,
+                             static_cast<double*>(d_adj_work), static_cast<cudaStream_t>(stream));
+    return cuda_check(nullptr, "adjoint init launch");
+}
+
+lbm_status lbm_adjoint_theta(const lbm_params* p, void* d_adj_work, double* out, void* stream) {
+    if (const char* m = check_adjoint(p)) return fail(nullptr, check_params(p) ? LBM_ERR_ARG : LBM_ERR_STATE, m);
+    if (!d_adj_work || !out) return fail(nullptr, LBM_ERR_ARG, "NULL buffer");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double* partials = static_cast<double*>(d_adj_work);
+    double* dout = partials + (size_t)lbm::adjoint_blocks() * lbm::adjoint_ntheta();
+    cudaGetLastError();
+    lbm::launch_theta_final(partials, dout, s);
+    lbm_status st = cuda_check(nullptr, "adjoint theta launch");
+    if (st != LBM_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(out, dout, lbm::adjoint_ntheta() * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(nullptr, LBM_ERR_CUDA, std::string("adjoint theta copy: ") + cudaGetErrorString(e));
     return LBM_OK;
 }
 
@@ -333,7 +478,7 @@ const char* lbm_last_error(const lbm_ctx* c) {
 }
 
 const char* lbm_build_info(void) {
-    return "gplbm sm_103a: AA-pattern fused collide-stream; storage f64/f32/f16/bf16; D2Q5/D3Q7 + D3Q19";
+    return "gplbm sm_103a: fused collide-stream (AA in place; two-buffer z-marching with flow); storage f64/f32/f16/bf16; D2Q5/D3Q7 + D3Q19";
 }
 
 }  // extern "C"

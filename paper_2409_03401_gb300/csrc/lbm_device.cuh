@@ -38,7 +38,7 @@ struct StateView {
     void* g;      // Q planes
     void* hA;
     void* hB;
-    float* rest;  // 3 planes (g_0, hA_0, hB_0) for 16-bit storage, else nullptr
+    float* rest;  // 4 FP32 planes (g_0, hA_0, hB_0, f_0) for 16-bit storage, else nullptr
 };
 
 enum { LAT_D2Q5 = 0, LAT_D3Q7 = 1 };
@@ -103,6 +103,13 @@ template <class T> struct Codec {
     __device__ static typename RealOf<T>::type load(const T* p, double, const DevParams&) { return *p; }
     template <int SET>
     __device__ static void store(T* p, typename RealOf<T>::type v, double, const DevParams&) { *p = v; }
+    // store and return what rounding removed (nothing here)
+    template <int SET>
+    __device__ static typename RealOf<T>::type store_residual(T* p, typename RealOf<T>::type v, double w,
+                                                              const DevParams& P) {
+        *p = v;
+        return typename RealOf<T>::type(0);
+    }
 };
 
 __device__ inline float to_f(__half v) { return __half2float(v); }
@@ -121,12 +128,23 @@ template <class H> struct Codec16 {
         return float(w) * (q * (1.0f / kHScale));
     }
     template <int SET>
-    __device__ static void store(H* p, float v, double w, const DevParams& P) {
+    __device__ static H encode(float v, double w, const DevParams& P) {
         float q = v * float(1.0 / w);
         if (SET == SET_F) q *= float(P.f_scale);
         else if (SET == SET_G) q -= 0.5f;
         else q *= kHScale;
-        *p = from_f<H>(q);
+        return from_f<H>(q);
+    }
+    template <int SET>
+    __device__ static void store(H* p, float v, double w, const DevParams& P) { *p = encode<SET>(v, w, P); }
+    // Store and return the rounding residual v - decode(encode(v)). The caller adds the
+    // residuals of a node's moving populations to its FP32 rest population, so the node's
+    // sum over k (phi, c, p_h) is kept to FP32 accuracy and rounding cannot act as a source.
+    template <int SET>
+    __device__ static float store_residual(H* p, float v, double w, const DevParams& P) {
+        const H h = encode<SET>(v, w, P);
+        *p = h;
+        return v - load<SET>(&h, w, P);
     }
 };
 template <> struct Codec<__half> : Codec16<__half> {};
@@ -140,9 +158,10 @@ template <class R> __device__ __forceinline__ R interp_p(R f) { return f * f * (
 template <class R> __device__ __forceinline__ R interp_dp(R f) { return R(6) * f * (R(1) - f); }
 template <class R> __device__ __forceinline__ R dwell_d(R f) { return R(16) * f * (R(1) - f) * (R(1) - R(2) * f); }
 
-// Eq. 33 written as mu = c - c_0^eq - p(phi) (c_1^eq - c_0^eq), since p(1 - phi) = 1 - p(phi)
-template <class R> __device__ __forceinline__ R closure(R c, R p, int a, const DevParams& P) {
-    return c - R(P.c0[a]) - p * R(P.dc[a]);
+// Eq. 33 written as mu = (c - c_0^eq) - p(phi) (c_1^eq - c_0^eq), since p(1 - phi) = 1 - p(phi).
+// The kernels carry the composition as its deviation dc = c - c_0^eq (see the h_0 storage).
+template <class R> __device__ __forceinline__ R closure_dev(R dc, R p, int a, const DevParams& P) {
+    return dc - p * R(P.dc[a]);
 }
 // Eq. 35 with Delta omega of Eq. 20 = sum mu (c_1^eq - c_0^eq)
 template <class R> __device__ __forceinline__ R source(R phi, R muA, R muB, const DevParams& P) {
@@ -153,46 +172,13 @@ template <class R> __device__ __forceinline__ R source(R phi, R muA, R muB, cons
 
 // ------------------------------------------------------------------------------------
 // Addressing. Node index of (x, y, z) with x fastest.
-__device__ __forceinline__ long long node_of(int x, int y, int z, const DevParams& P) {
-    return ((long long)z * P.ny + y) * P.nx + x;
+// Node indices are 32-bit (the host rejects lattices of 2^31 nodes or more); offsets into
+// the population planes are formed in 64 bits.
+__device__ __forceinline__ int node_of(int x, int y, int z, const DevParams& P) {
+    return (z * P.ny + y) * P.nx + x;
 }
-// Shift one coordinate by d; false when the result lies beyond a wall (no wrap there).
-__device__ __forceinline__ bool shift1(int& c, int d, int n, int wall) {
-    c += d;
-    if (c < 0) { if (wall) return false; c += n; }
-    else if (c >= n) { if (wall) return false; c -= n; }
-    return true;
-}
-__device__ __forceinline__ bool neighbour(int x, int y, int z, int dx, int dy, int dz,
-                                          const DevParams& P, long long& out) {
-    bool ok = shift1(x, dx, P.nx, P.wall_x);
-    ok = shift1(y, dy, P.ny, 0) && ok;
-    ok = shift1(z, dz, P.nz, P.wall_z) && ok;
-    out = node_of(x, y, z, P);
-    return ok;
-}
-
-// AA pattern. Even step: population k of node x is read from slot k of x and its
-// post-collision value written to slot opp(k) of x. Odd step: incoming k is read from
-// slot opp(k) of x - e_k and the post-collision value written to slot k of x + e_k;
-// across a wall both fall back to node x with the slots exchanged (half-way bounce-back).
-struct Slot { long long node; int slot; };
-
-__device__ __forceinline__ Slot read_slot(bool odd, int k, int ex, int ey, int ez,
-                                          int x, int y, int z, long long self, const DevParams& P) {
-    if (!odd || k == 0) return {self, k};
-    long long nb;
-    if (neighbour(x, y, z, -ex, -ey, -ez, P, nb)) return {nb, opp(k)};
-    return {self, k};
-}
-__device__ __forceinline__ Slot write_slot(bool odd, int k, int ex, int ey, int ez,
-                                           int x, int y, int z, long long self, const DevParams& P) {
-    if (k == 0) return {self, 0};
-    if (!odd) return {self, opp(k)};
-    long long nb;
-    if (neighbour(x, y, z, ex, ey, ez, P, nb)) return {nb, k};
-    return {self, opp(k)};
-}
+// Population slot of a node: element node of population plane slot.
+struct Slot { int node; int slot; };
 
 // Load / store one population of a scalar set, with the 16-bit rest planes in FP32.
 template <class T, int SET, int LAT>
@@ -206,6 +192,13 @@ __device__ __forceinline__ void
 store_scalar(T* base, float* rest, int k, Slot s, typename RealOf<T>::type v, const DevParams& P) {
     if (is16<T>() && k == 0) { rest[s.node] = float(v); return; }
     Codec<T>::template store<SET>(base + (long long)s.slot * P.plane + s.node, v, Scalar<LAT>::w(k), P);
+}
+// moving population k > 0; returns the rounding residual of 16-bit storage (0 otherwise)
+template <class T, int SET, int LAT>
+__device__ __forceinline__ typename RealOf<T>::type
+store_moving(T* base, int k, Slot s, typename RealOf<T>::type v, const DevParams& P) {
+    return Codec<T>::template store_residual<SET>(base + (long long)s.slot * P.plane + s.node, v,
+                                                  Scalar<LAT>::w(k), P);
 }
 
 }  // namespace lbm

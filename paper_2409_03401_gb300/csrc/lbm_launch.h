@@ -13,17 +13,32 @@ namespace lbm {
 
 struct FieldPtrs { void* p[LBM_NFIELDS_DEV]; };
 
-#define LBM_DECLARE_LAUNCHERS(SUFFIX)                                                                 \
-    void launch_init_##SUFFIX(const DevParams&, const StateView&, int lat, bool flow,                 \
-                              const double*, const double*, const double*, cudaStream_t);             \
-    void launch_phi_##SUFFIX(const DevParams&, const StateView&, int lat, bool odd, void* phi,        \
-                             cudaStream_t);                                                           \
-    void launch_step_##SUFFIX(const DevParams&, const StateView&, int lat, bool flow, bool odd,       \
-                              void* phi, cudaStream_t);                                               \
-    void launch_fields_##SUFFIX(const DevParams&, const StateView&, int lat, bool flow, bool odd,     \
-                                void* phi, FieldPtrs, cudaStream_t);                                  \
-    void launch_reduce_##SUFFIX(const DevParams&, const StateView&, int lat, bool flow, bool odd,     \
+// streaming modes (see lbm_kernels.cuh)
+constexpr int kModeAAEven = 0, kModeAAOdd = 1, kModePull = 2;
+
+#define LBM_DECLARE_LAUNCHERS(SUFFIX)                                                                   \
+    void launch_init_##SUFFIX(const DevParams&, const StateView&, int lat, bool flow, bool pull,         \
+                              const double*, const double*, const double*, cudaStream_t);                \
+    void launch_phi_##SUFFIX(const DevParams&, const StateView&, int lat, int mode, void* phi,           \
+                             cudaStream_t);                                                              \
+    void launch_step_##SUFFIX(const DevParams&, const StateView&, const StateView&, int lat, bool flow, \
+                              int mode, void* phi, cudaStream_t);                                        \
+    void launch_fused_##SUFFIX(const DevParams&, const StateView&, const StateView&, int zchunk,        \
+                               cudaStream_t);                                                            \
+    void launch_fields_##SUFFIX(const DevParams&, const StateView&, int lat, bool flow, int mode,        \
+                                void* phi, FieldPtrs, cudaStream_t);                                     \
+    void launch_reduce_##SUFFIX(const DevParams&, const StateView&, int lat, bool flow, int mode,        \
                                 void* phi, double* partials, int nblocks, cudaStream_t);
+
+void launch_adjoint_step(const DevParams&, const StateView&, int storage, int lat, bool odd, const void* lam_next,
+                         void* lam, double* partials, cudaStream_t);
+void launch_adjoint_seed(const DevParams&, const StateView&, int storage, int lat, bool odd, const void* phib,
+                         const void* muAb, const void* muBb, void* lam, double* partials, cudaStream_t);
+void launch_adjoint_init(const DevParams&, int storage, int lat, const double* phi0, const double* cA0,
+                         const double* cB0, const void* lam, double* phi0b, double* partials, cudaStream_t);
+void launch_theta_final(const double* partials, double* out, cudaStream_t);
+int adjoint_blocks();
+int adjoint_ntheta();
 
 LBM_DECLARE_LAUNCHERS(f64)
 LBM_DECLARE_LAUNCHERS(f32)

@@ -43,10 +43,15 @@ def test_sizes_and_validation_on_the_host(lib):
     cp = _lib.make_params(p)
     n = 512 ** 3
     state = lib.lbm_state_bytes(ctypes.byref(cp))
-    assert state == 40 * 4 * n                         # 19 + 3 x 7 FP32 planes
+    assert state == 2 * 40 * 4 * n                     # two copies of 19 + 3 x 7 FP32 planes
+    inplace = lib.lbm_state_bytes(ctypes.byref(_lib.make_params(p.with_(inplace=True))))
+    assert inplace == 40 * 4 * n                       # one in-place AA copy
     p16 = p.with_(storage="f16")
     s16 = lib.lbm_state_bytes(ctypes.byref(_lib.make_params(p16)))
-    assert s16 == 40 * 2 * n + 3 * 4 * n               # 16-bit planes + FP32 rest planes
+    assert s16 == 2 * (40 * 2 * n + 4 * 4 * n)         # 16-bit planes + 4 FP32 rest planes, two copies
+    noflow = lib.lbm_state_bytes(ctypes.byref(_lib.make_params(p.with_(flow=False))))
+    assert noflow == 21 * 4 * n                        # scalars only: always one in-place copy
+    assert lib.lbm_state_bytes(ctypes.byref(_lib.make_params(p.with_(nx=2048, ny=1024, nz=1024)))) == 0
     bad = _lib.make_params(p.with_(nz=70000))
     assert lib.lbm_state_bytes(ctypes.byref(bad)) == 0
     ctx = ctypes.c_void_p()

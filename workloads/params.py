@@ -29,6 +29,7 @@ class LBMParams:
     wall_x: bool = False           # half-way bounce-back planes at x = -1/2 and x = nx - 1/2
     wall_z: bool = False           # half-way bounce-back planes at z = -1/2 and z = nz - 1/2
     source_off: bool = False       # test switch: drop the phase-field source (pure advection-diffusion)
+    inplace: bool = False          # flow on the GPU: one in-place AA copy + phi pass instead of two copies
     W: float = 3.0
     lam: float = 155.95
     M_phi: float = 0.12
