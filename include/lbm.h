@@ -196,6 +196,22 @@ lbm_status lbm_adjoint_init(const lbm_params* p, const double* d_phi0, const dou
  * Synchronises the stream. */
 lbm_status lbm_adjoint_theta(const lbm_params* p, void* d_adj_work, double* out, void* stream);
 
+/* Allocation-free FP64 diagnostics. The paper has no counterpart: this is for callers that
+ * cannot allocate device memory at the time they need the sums (for example a host
+ * application that hands this library its state buffer but owns every allocation, or a
+ * real-time loop where allocation is forbidden after start-up). Same results as
+ * lbm_reduce for the state copy d_state holds at time t (the buffer lbm_init was given),
+ * but the reduction's scratch (block partials, results, and with flow the phi field) lives
+ * in a file-scope device array of 4 MiB that every GPU loading this library holds until
+ * the process exits. Lattices whose scratch exceeds 4 MiB (flow lattices above about one
+ * million nodes) are rejected with LBM_ERR_ARG. The call allocates nothing. The first call
+ * on each device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture. Every call shares the
+ * array and leaves its contents behind; the kernels overwrite all of it that they read, so
+ * nothing needs clearing, but calls that overlap on the GPU (other streams, other host
+ * threads) race on it. Synchronises the stream. */
+lbm_status lbm_reduce_static(const lbm_params* p, const void* d_state, int64_t t, double* out, void* stream);
+
 /* Release the context (host memory only; device buffers remain the caller's). */
 lbm_status lbm_destroy(lbm_ctx* ctx);
 

@@ -1,6 +1,7 @@
 // C-ABI entry points (include/lbm.h): validation, buffer layout, launch sequencing.
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -482,3 +483,72 @@ const char* lbm_build_info(void) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------
+// Allocation-free variant of lbm_reduce (see include/lbm.h): its scratch lives in this
+// file-scope device array instead of the caller's work buffer.
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(4) << 20;
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mu;
+void* g_static_ptr[64] = {};
+
+// Device address of g_static_scratch on the current device. In host code the array's name
+// only stands in for the symbol, so the address is looked up once per device, with that
+// device current, and cached.
+lbm_status static_scratch(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(nullptr, LBM_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (dev < 0 || dev >= 64) return fail(nullptr, LBM_ERR_ARG, "device index beyond 63");
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(nullptr, LBM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        g_static_ptr[dev] = p;
+    }
+    *out = g_static_ptr[dev];
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" lbm_status lbm_reduce_static(const lbm_params* p, const void* d_state, int64_t t, double* out,
+                                        void* stream) {
+    if (const char* m = check_params(p)) return fail(nullptr, LBM_ERR_ARG, m);
+    if (!d_state || !out || t < 0) return fail(nullptr, LBM_ERR_ARG, "d_state and out must be non-NULL, t >= 0");
+    if ((uintptr_t)d_state % kAlign) return fail(nullptr, LBM_ERR_ARG, "d_state must be 256-byte aligned");
+    const Layout L = layout_of(p);
+    if (L.work > kStaticScratchBytes)
+        return fail(nullptr, LBM_ERR_ARG,
+                    "lbm_reduce_static: this lattice needs " + std::to_string(L.work) +
+                        " bytes of scratch (the phi field of a flow lattice) but the static array holds " +
+                        std::to_string(kStaticScratchBytes) + "; use lbm_reduce with a work buffer");
+    void* scratch = nullptr;
+    lbm_status s = static_scratch(&scratch);
+    if (s != LBM_OK) return s;
+    char* w = static_cast<char*>(scratch);
+    const DevParams dp = dev_params(p, L);
+    void* copy = static_cast<char*>(const_cast<void*>(d_state)) + ((L.two && (t & 1)) ? L.copy : 0);
+    const StateView st = view_of(p, L, copy);
+    const int mode = L.two ? lbm::kModePull : ((t & 1) ? lbm::kModeAAOdd : lbm::kModeAAEven);
+    double* partials = reinterpret_cast<double*>(w + L.off_partials);
+    double* dout = reinterpret_cast<double*>(w + L.off_out);
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    cudaGetLastError();
+    LBM_DISPATCH(p->storage, launch_reduce, dp, st, p->lattice, p->flow != 0, mode, w + L.off_phi, partials,
+                 kRedBlocks, cs);
+    reduce_final<<<1, 256, 0, cs>>>(partials, kRedBlocks, dout);
+    s = cuda_check(nullptr, "static reduce launch");
+    if (s != LBM_OK) return s;
+    cudaError_t e = cudaMemcpyAsync(out, dout, LBM_NRED * sizeof(double), cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) return fail(nullptr, LBM_ERR_CUDA, std::string("static reduce copy: ") + cudaGetErrorString(e));
+    if (out[LBM_RED_NONFINITE] != 0.0)
+        return fail(nullptr, LBM_ERR_UNSTABLE, "non-finite moments in the state (unstable run)");
+    return LBM_OK;
+}
