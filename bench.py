@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-planes", type=int, default=16)
     ap.add_argument("--cpu-sample-steps", type=int, default=6)
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle leg (profiling runs)")
     return ap.parse_args()
 
 
@@ -262,7 +263,7 @@ def gb300(args):
                    "l2": "state 21.5 GB >> 129 MB L2, no flush", "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "step_kernel<float, D3Q7, flow> (fused collide+stream)",
+                     "kernel": "fused_flow_kernel<float> (z-marching fused phi + collide + stream)",
                      "alg_bytes_per_launch": bytes_step, "ms_per_launch": ms_step,
                      "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
                      "whole_step_frac": bytes_step / (ms / args.steps / 1e3) / 1e9 / peak,
@@ -296,7 +297,7 @@ def gb300(args):
     if not args.no_e2e:
         out["e2e"] = run_e2e(p, init, args.steps, device)
 
-    if rank == 0 and ws == 1:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(init, p, args.cpu_sample_planes, args.cpu_sample_steps)
     if rank == 0:
         print(json.dumps(out))

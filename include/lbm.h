@@ -72,7 +72,7 @@ typedef struct lbm_params {
     double nu;               /* kinematic viscosity, tau_f = nu / c_s^2 (Eq. 36) */
     double sigma;            /* surface tension in Eq. 34 */
     double g[3];             /* buoyancy per unit phi: F_g = phi * g (§2.5, Delta rho g / rho_0) */
-    double f_scale;          /* 16-bit storage: scale of f_k / w_k (power of two recommended) */
+    double f_scale;          /* 16-bit storage scale of f_k / w_k: 0 or 1024 (fixed at 1024) */
 } lbm_params;
 
 /* Indices of lbm_fields outputs. */
@@ -185,6 +185,14 @@ lbm_status lbm_adjoint_seed(const lbm_params* p, const void* d_state, int64_t t,
 /* Lambda_t (d_lam) from Lambda_{t+1} (d_lam_next) at the state copy of time t. */
 lbm_status lbm_adjoint_step(const lbm_params* p, const void* d_state, int64_t t, const void* d_lam_next,
                             void* d_lam, void* d_adj_work, void* stream);
+
+/* One checkpoint segment of the reverse sweep in a single call: the states t0+1 .. t0+n-1
+ * are recomputed out of place from the checkpoint in copy 0 of d_ring (n state copies,
+ * lbm_copy_bytes apart) into copies 1 .. n-1, then the n reverse steps t0+n-1 .. t0 run from
+ * Lambda_{t0+n} in d_lam, alternating with d_lam_tmp. *which receives 0 when Lambda_{t0}
+ * ends in d_lam and 1 when it ends in d_lam_tmp. d_work as for lbm_init. */
+lbm_status lbm_adjoint_segment(const lbm_params* p, void* d_ring, int64_t t0, int n, void* d_lam,
+                               void* d_lam_tmp, void* d_adj_work, void* d_work, void* stream, int* which);
 
 /* dL/dphi_0 (FP64, per node) from Lambda_0 through the initial populations of lbm_init;
  * adds the M_phi part of the initial source to the partials. */

@@ -74,6 +74,8 @@ def load():
         "lbm_adjoint_reset": (ctypes.c_int, [P, vp, vp]),
         "lbm_adjoint_seed": (ctypes.c_int, [P, vp, ctypes.c_int64, vp, vp, vp, vp, vp, vp]),
         "lbm_adjoint_step": (ctypes.c_int, [P, vp, ctypes.c_int64, vp, vp, vp, vp]),
+        "lbm_adjoint_segment": (ctypes.c_int, [P, vp, ctypes.c_int64, ctypes.c_int, vp, vp, vp, vp, vp,
+                                                ctypes.POINTER(ctypes.c_int)]),
         "lbm_adjoint_init": (ctypes.c_int, [P, vp, vp, vp, vp, vp, vp, vp]),
         "lbm_adjoint_theta": (ctypes.c_int, [P, vp, ctypes.POINTER(ctypes.c_double), vp]),
         "lbm_reduce_static": (ctypes.c_int, [P, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), vp]),
@@ -93,7 +95,7 @@ def exported_symbols():
     return ["lbm_state_bytes", "lbm_work_bytes", "lbm_init", "lbm_attach", "lbm_step", "lbm_time",
             "lbm_fields", "lbm_reduce", "lbm_profile_begin", "lbm_profile_end", "lbm_kernels_per_step",
             "lbm_copy_bytes", "lbm_step_buffers", "lbm_adjoint_bytes", "lbm_adjoint_work_bytes",
-            "lbm_adjoint_reset", "lbm_adjoint_seed", "lbm_adjoint_step", "lbm_adjoint_init",
+            "lbm_adjoint_reset", "lbm_adjoint_seed", "lbm_adjoint_step", "lbm_adjoint_segment", "lbm_adjoint_init",
             "lbm_adjoint_theta", "lbm_reduce_static", "lbm_destroy", "lbm_last_error", "lbm_build_info"]
 
 

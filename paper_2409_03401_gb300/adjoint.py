@@ -4,10 +4,10 @@
 steps from the initial phase field ``phi0`` with theta = (D_0, D_1, M_phi) (D_pi is the
 mobility of both components in phase pi) and returns (phi, mu^A, mu^B) of the final time
 level. Forward: the state is checkpointed every K steps. Backward: for each segment in
-reverse order, the K states are recomputed out of place from the checkpoint into a ring
-(lbm_step_buffers), then the hand-written adjoint kernels run from the segment's last
-step down to its first (lbm_adjoint_step); lbm_adjoint_init maps the adjoint of the
-initial populations to dL/dphi0. Every step runs in the library's CUDA kernels.
+reverse order, one lbm_adjoint_segment call recomputes the K states out of place from the
+checkpoint into a ring, then runs the hand-written adjoint kernels from the segment's last
+step down to its first; lbm_adjoint_init maps the adjoint of the initial populations to
+dL/dphi0. Every step runs in the library's CUDA kernels.
 """
 import ctypes
 
@@ -70,16 +70,15 @@ class CoupledRun(torch.autograd.Function):
         _lib.check(lib.lbm_adjoint_seed(ctypes.byref(cp), _vp(sim.state), steps, _vp(g[0]), _vp(g[1]), _vp(g[2]),
                                         _vp(lam), _vp(adj_work), stream))
         copy = lib.lbm_copy_bytes(ctypes.byref(cp))
-        ring = [torch.empty(copy, dtype=torch.uint8, device=device) for _ in range(min(K, steps))]
+        ring = torch.empty(min(K, steps) * copy, dtype=torch.uint8, device=device)
+        which = ctypes.c_int(0)
         for t0, ck in reversed(ctx.ckpts):
             n = min(K, steps - t0)
-            ring[0].copy_(ck)
-            for j in range(1, n):
-                _lib.check(lib.lbm_step_buffers(ctypes.byref(cp), _vp(ring[j - 1]), _vp(ring[j]), t0 + j - 1,
-                                                _vp(sim.work), stream))
-            for t in range(t0 + n - 1, t0 - 1, -1):
-                _lib.check(lib.lbm_adjoint_step(ctypes.byref(cp), _vp(ring[t - t0]), t, _vp(lam), _vp(lam2),
-                                                _vp(adj_work), stream))
+            ring[:copy].copy_(ck)
+            # recompute the segment's states and sweep it in reverse (one library call)
+            _lib.check(lib.lbm_adjoint_segment(ctypes.byref(cp), _vp(ring), t0, n, _vp(lam), _vp(lam2),
+                                               _vp(adj_work), _vp(sim.work), stream, ctypes.byref(which)))
+            if which.value == 1:
                 lam, lam2 = lam2, lam
         phi0d, cA0d, cB0d = ctx.init
         phi0b = torch.empty_like(phi0d)

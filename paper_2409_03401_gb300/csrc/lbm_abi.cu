@@ -51,7 +51,7 @@ const char* check_params(const lbm_params* p) {
         for (int a = 0; a < 2; ++a)
             if (!(p->M[ph][a] > 0)) return "mobilities M must be > 0";
     if (p->flow && !(p->nu > 0)) return "nu must be > 0 with flow";
-    if (is16(p->storage) && p->f_scale < 0) return "f_scale must be >= 0 (0 selects 1024)";
+    if (!(p->f_scale == 0.0 || p->f_scale == 1024.0)) return "f_scale must be 0 or 1024 (the fixed 16-bit scale)";
     return nullptr;
 }
 
@@ -164,6 +164,26 @@ __global__ void reduce_final(const double* __restrict__ partials, int nblocks, d
     if (threadIdx.x < LBM_NRED) out[threadIdx.x] = sm[threadIdx.x][0];
 }
 
+// Views of one state copy starting at base, with the pointer of every population plane.
+StateView view_of(const lbm_params* p, const Layout& L, void* base) {
+    StateView v{};
+    char* s = static_cast<char*>(base);
+    const size_t pb = (size_t)L.plane * storage_size(p->storage);
+    const int Q = scalar_q(p->lattice);
+    v.f = p->flow ? s + L.off_f : nullptr;
+    v.g = s + L.off_g;
+    v.hA = s + L.off_hA;
+    v.hB = s + L.off_hB;
+    v.rest = is16(p->storage) ? reinterpret_cast<float*>(s + L.off_rest) : nullptr;
+    for (int k = 0; k < 19; ++k) v.plane[k] = p->flow ? s + L.off_f + k * pb : nullptr;
+    for (int k = 0; k < Q; ++k) {
+        v.plane[lbm::kPlaneG + k] = s + L.off_g + k * pb;
+        v.plane[lbm::kPlaneHA + k] = s + L.off_hA + k * pb;
+        v.plane[lbm::kPlaneHB + k] = s + L.off_hB + k * pb;
+    }
+    return v;
+}
+
 lbm_status bind(const lbm_params* p, void* d_state, void* d_work, void* stream, lbm_ctx** out) {
     if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
     *out = nullptr;
@@ -176,34 +196,14 @@ lbm_status bind(const lbm_params* p, void* d_state, void* d_work, void* stream, 
     c->p = *p;
     c->L = layout_of(p);
     c->dp = dev_params(p, c->L);
-    for (int cp = 0; cp < (c->L.two ? 2 : 1); ++cp) {
-        char* s = static_cast<char*>(d_state) + cp * c->L.copy;
-        StateView& v = cp == 0 ? c->st : c->st1;
-        v.f = p->flow ? s + c->L.off_f : nullptr;
-        v.g = s + c->L.off_g;
-        v.hA = s + c->L.off_hA;
-        v.hB = s + c->L.off_hB;
-        v.rest = is16(p->storage) ? reinterpret_cast<float*>(s + c->L.off_rest) : nullptr;
-    }
-    if (!c->L.two) c->st1 = c->st;
+    c->st = view_of(p, c->L, d_state);
+    c->st1 = c->L.two ? view_of(p, c->L, static_cast<char*>(d_state) + c->L.copy) : c->st;
     c->work = static_cast<char*>(d_work);
     c->stream = static_cast<cudaStream_t>(stream);
     c->t = 0;
     c->err = "no error";
     *out = c;
     return LBM_OK;
-}
-
-// Views of one state copy starting at base.
-StateView view_of(const lbm_params* p, const Layout& L, void* base) {
-    StateView v{};
-    char* s = static_cast<char*>(base);
-    v.f = p->flow ? s + L.off_f : nullptr;
-    v.g = s + L.off_g;
-    v.hA = s + L.off_hA;
-    v.hB = s + L.off_hB;
-    v.rest = is16(p->storage) ? reinterpret_cast<float*>(s + L.off_rest) : nullptr;
-    return v;
 }
 
 // State view holding time level t and the streaming mode that reads it.
@@ -438,6 +438,28 @@ lbm_status lbm_adjoint_step(const lbm_params* p, const void* d_state, int64_t t,
                              (t & 1) != 0, d_lam_next, d_lam, static_cast<double*>(d_adj_work),
                              static_cast<cudaStream_t>(stream));
     return cuda_check(nullptr, "adjoint step launch");
+}
+
+lbm_status lbm_adjoint_segment(const lbm_params* p, void* d_ring, int64_t t0, int n, void* d_lam, void* d_lam_tmp,
+                               void* d_adj_work, void* d_work, void* stream, int* which) {
+    if (const char* m = check_adjoint(p)) return fail(nullptr, check_params(p) ? LBM_ERR_ARG : LBM_ERR_STATE, m);
+    if (!d_ring || !d_lam || !d_lam_tmp || !d_adj_work || !which || t0 < 0 || n < 1)
+        return fail(nullptr, LBM_ERR_ARG, "NULL buffer, t0 < 0 or n < 1");
+    const Layout L = layout_of(p);
+    char* ring = static_cast<char*>(d_ring);
+    for (int j = 1; j < n; ++j) {
+        lbm_status s = lbm_step_buffers(p, ring + (j - 1) * L.copy, ring + j * L.copy, t0 + j - 1, d_work, stream);
+        if (s != LBM_OK) return s;
+    }
+    void* cur = d_lam;
+    void* nxt = d_lam_tmp;
+    for (int j = n - 1; j >= 0; --j) {
+        lbm_status s = lbm_adjoint_step(p, ring + j * L.copy, t0 + j, cur, nxt, d_adj_work, stream);
+        if (s != LBM_OK) return s;
+        void* t = cur; cur = nxt; nxt = t;
+    }
+    *which = cur == d_lam ? 0 : 1;
+    return LBM_OK;
 }
 
 lbm_status lbm_adjoint_init(const lbm_params* p, const double* d_phi0, const double* d_cA0, const double* d_cB0,

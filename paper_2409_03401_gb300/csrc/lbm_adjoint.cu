@@ -154,17 +154,22 @@ adjoint_step_kernel(const DevParams P, const StateView st, const typename RealOf
         int x, y, z;
         coords(id, P, x, y, z);
         const int self = int(id);
-        AddrWrap<MODE> ad;
+        Addr<MODE> ad;
         ad.nb.init(x, y, z, P);
         ad.self = self;
         Node<T, LAT, false> nd;
         nd.gather(st, ad, P);
         nd.moments(P);
+        // where the forward step streams P*_t(x, k): the AA odd-step scatter pattern,
+        // which sends it to slot k of x + e_k, or to slot opp(k) of x across a wall
+        Addr<AA_ODD> fwd;
+        fwd.nb = ad.nb;
+        fwd.self = self;
         R ag[Q], ahA[Q], ahB[Q];
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
             // where P*_t(x, k) streams to: slot k of x + e_k, or slot opp(k) of x across a wall
-            const Slot s = dst_slot<AA_ODD>(k, L::ex(k), L::ey(k), L::ez(k), ad.nb, self);
+            const Slot s = fwd.dst(k, L::ex(k), L::ey(k), L::ez(k));
             ag[k] = lam_next[(long long)(0 * Q + s.slot) * P.plane + s.node];
             ahA[k] = lam_next[(long long)(1 * Q + s.slot) * P.plane + s.node];
             ahB[k] = lam_next[(long long)(2 * Q + s.slot) * P.plane + s.node];
@@ -196,7 +201,7 @@ adjoint_seed_kernel(const DevParams P, const StateView st, const typename RealOf
         int x, y, z;
         coords(id, P, x, y, z);
         const int self = int(id);
-        AddrWrap<MODE> ad;
+        Addr<MODE> ad;
         ad.nb.init(x, y, z, P);
         ad.self = self;
         Node<T, LAT, false> nd;

@@ -32,13 +32,18 @@ struct DevParams {
 };
 
 // Pointers of one state buffer: population planes in the storage type, plus the FP32
-// rest-population planes used by 16-bit storage.
+// rest-population planes used by 16-bit storage. ``plane`` lists every population plane
+// (f_0..f_18, then g, h^A, h^B from kPlaneG, kPlaneHA, kPlaneHB) so that a kernel can
+// address population k of node n as plane[k] + n, the pointer coming straight from the
+// kernel's parameter space.
+constexpr int kPlaneG = 19, kPlaneHA = 26, kPlaneHB = 33, kPlanes = 40;
 struct StateView {
     void* f;      // 19 planes (flow only)
     void* g;      // Q planes
     void* hA;
     void* hB;
     float* rest;  // 4 FP32 planes (g_0, hA_0, hB_0, f_0) for 16-bit storage, else nullptr
+    void* plane[kPlanes];
 };
 
 enum { LAT_D2Q5 = 0, LAT_D3Q7 = 1 };
@@ -95,7 +100,8 @@ template <> struct RealOf<double> { using type = double; };
 
 // Which population set a plane belongs to, for the 16-bit deviation encoding.
 enum { SET_F = 0, SET_G = 1, SET_H = 2 };
-constexpr float kHScale = 64.0f;
+constexpr float kHScale = 64.0f;       // 16-bit h_k / w_k scale (h_k ~ w_k mu, mu ~ 1e-3..1e-2)
+constexpr float kFScale = 1024.0f;     // 16-bit f_k / w_k scale (f_k ~ w_k (p_h + 3 e.u) ~ 1e-3 w_k)
 
 template <class T> struct Codec {
     // plain FP32 / FP64 storage
@@ -122,17 +128,17 @@ template <class H> struct Codec16 {
     // q = P / w - ref, scaled: f (ref 0, x f_scale), g (ref 1/2), h (ref 0, x 64)
     template <int SET>
     __device__ static float load(const H* p, double w, const DevParams& P) {
-        float q = to_f(*p);
-        if (SET == SET_F) return float(w) * (q * float(P.inv_f_scale));
+        const float q = to_f(*p);
+        if (SET == SET_F) return q * float(w / kFScale);
         if (SET == SET_G) return float(w) * (q + 0.5f);
-        return float(w) * (q * (1.0f / kHScale));
+        return q * float(w / kHScale);
     }
     template <int SET>
     __device__ static H encode(float v, double w, const DevParams& P) {
-        float q = v * float(1.0 / w);
-        if (SET == SET_F) q *= float(P.f_scale);
-        else if (SET == SET_G) q -= 0.5f;
-        else q *= kHScale;
+        float q;
+        if (SET == SET_F) q = v * float(kFScale / w);
+        else if (SET == SET_G) q = v * float(1.0 / w) - 0.5f;
+        else q = v * float(kHScale / w);
         return from_f<H>(q);
     }
     template <int SET>
@@ -180,25 +186,33 @@ __device__ __forceinline__ int node_of(int x, int y, int z, const DevParams& P) 
 // Population slot of a node: element node of population plane slot.
 struct Slot { int node; int slot; };
 
-// Load / store one population of a scalar set, with the 16-bit rest planes in FP32.
-template <class T, int SET, int LAT>
-__device__ __forceinline__ typename RealOf<T>::type
-load_scalar(const T* base, const float* rest, int k, Slot s, const DevParams& P) {
-    if (is16<T>() && k == 0) return rest[s.node];
-    return Codec<T>::template load<SET>(base + (long long)s.slot * P.plane + s.node, Scalar<LAT>::w(k), P);
+// Element of population slot s.slot (k or opp(k): the slot is one of these two constants) of
+// the set whose first plane is B, at node s.node.
+template <class T, int B>
+__device__ __forceinline__ T* element(const StateView& st, int k, Slot s) {
+    T* base = static_cast<T*>(s.slot == k ? st.plane[B + k] : st.plane[B + opp(k)]);
+    return base + s.node;
 }
-template <class T, int SET, int LAT>
-__device__ __forceinline__ void
-store_scalar(T* base, float* rest, int k, Slot s, typename RealOf<T>::type v, const DevParams& P) {
-    if (is16<T>() && k == 0) { rest[s.node] = float(v); return; }
-    Codec<T>::template store<SET>(base + (long long)s.slot * P.plane + s.node, v, Scalar<LAT>::w(k), P);
+
+// Load / store one population of a scalar set (first plane B); with 16-bit storage the rest
+// population lives in FP32 rest plane RP (g: 0, h^A: 1, h^B: 2, f: 3).
+template <class T, int SET, int LAT, int B, int RP>
+__device__ __forceinline__ typename RealOf<T>::type load_scalar(const StateView& st, int k, Slot s,
+                                                                const DevParams& P) {
+    if (is16<T>() && k == 0) return st.rest[RP * P.plane + s.node];
+    return Codec<T>::template load<SET>(element<T, B>(st, k, s), Scalar<LAT>::w(k), P);
+}
+template <class T, int SET, int LAT, int B, int RP>
+__device__ __forceinline__ void store_scalar(const StateView& st, int k, Slot s, typename RealOf<T>::type v,
+                                             const DevParams& P) {
+    if (is16<T>() && k == 0) { st.rest[RP * P.plane + s.node] = float(v); return; }
+    Codec<T>::template store<SET>(element<T, B>(st, k, s), v, Scalar<LAT>::w(k), P);
 }
 // moving population k > 0; returns the rounding residual of 16-bit storage (0 otherwise)
-template <class T, int SET, int LAT>
-__device__ __forceinline__ typename RealOf<T>::type
-store_moving(T* base, int k, Slot s, typename RealOf<T>::type v, const DevParams& P) {
-    return Codec<T>::template store_residual<SET>(base + (long long)s.slot * P.plane + s.node, v,
-                                                  Scalar<LAT>::w(k), P);
+template <class T, int SET, int LAT, int B>
+__device__ __forceinline__ typename RealOf<T>::type store_moving(const StateView& st, int k, Slot s,
+                                                                 typename RealOf<T>::type v, const DevParams& P) {
+    return Codec<T>::template store_residual<SET>(element<T, B>(st, k, s), v, Scalar<LAT>::w(k), P);
 }
 
 }  // namespace lbm

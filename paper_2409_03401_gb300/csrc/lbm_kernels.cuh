@@ -19,72 +19,72 @@ namespace lbm {
 constexpr int kBlockX = 128;
 enum { AA_EVEN = 0, AA_ODD = 1, PULL = 2 };
 
-// Wrapped neighbour coordinates of one node, computed once per thread. c[a][1 + d] is the
-// coordinate x_a + d along axis a (d = -1, 0, 1) after the periodic wrap, or -1 where
-// x_a + d lies beyond a wall.
+// Wrapped neighbour coordinates of one node. c[a][1 + d] is the coordinate x_a + d along
+// axis a (d = -1, 0, 1) after the periodic wrap, or -1 where x_a + d lies beyond a wall;
+// row[iz][iy] = (z' ny + y') nx of the neighbouring rows (own plane beyond a wall). All
+// selects, no branches: warps straddling a domain edge do not diverge. init_xy() once per
+// (x, y) column and set_z() per plane let z-marching kernels skip the x/y part.
 struct Nbr {
     int c[3][3];
-    int row[3][3];  // (z' ny + y') nx for z' = c[2][iz] (own plane beyond a wall), y' = c[1][iy]
-    __device__ __forceinline__ void init(int x, int y, int z, const DevParams& P) {
-        const int n[3] = {P.nx, P.ny, P.nz};
-        const int w[3] = {P.wall_x, 0, P.wall_z};
-        const int v[3] = {x, y, z};
+    int row[3][3];
+    __device__ __forceinline__ static int wrap(int q, int n, int wall) {
+        return q < 0 ? (wall ? -1 : q + n) : (q >= n ? (wall ? -1 : q - n) : q);
+    }
+    __device__ __forceinline__ void init_xy(int x, int y, const DevParams& P) {
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-#pragma unroll
-            for (int d = -1; d <= 1; ++d) {
-                int q = v[a] + d;
-                if (q < 0) q = w[a] ? -1 : q + n[a];
-                else if (q >= n[a]) q = w[a] ? -1 : q - n[a];
-                c[a][d + 1] = q;
-            }
+        for (int d = -1; d <= 1; ++d) {
+            c[0][d + 1] = wrap(x + d, P.nx, P.wall_x);
+            c[1][d + 1] = wrap(y + d, P.ny, 0);
         }
+    }
+    __device__ __forceinline__ void set_z(int z, const DevParams& P) {
+#pragma unroll
+        for (int d = -1; d <= 1; ++d) c[2][d + 1] = wrap(z + d, P.nz, P.wall_z);
 #pragma unroll
         for (int iz = 0; iz < 3; ++iz)
 #pragma unroll
             for (int iy = 0; iy < 3; ++iy)
                 row[iz][iy] = ((c[2][iz] < 0 ? z : c[2][iz]) * P.ny + c[1][iy]) * P.nx;
     }
+    __device__ __forceinline__ void init(int x, int y, int z, const DevParams& P) {
+        init_xy(x, y, P);
+        set_z(z, P);
+    }
     // node x + (dx, dy, dz); false (and the node itself) when that lies beyond a wall
     __device__ __forceinline__ bool at(int dx, int dy, int dz, int self, int& out) const {
         const int xx = c[0][dx + 1], zz = c[2][dz + 1];
-        if (xx < 0 || zz < 0) { out = self; return false; }
-        out = row[dz + 1][dy + 1] + xx;
-        return true;
+        const bool in = (dx == 0 || xx >= 0) && (dz == 0 || zz >= 0);
+        out = in ? row[dz + 1][dy + 1] + xx : self;
+        return in;
     }
 };
 
-// Where population k of this node is read from / written to, for each streaming mode.
-// Across a wall both fall back to the node itself with k and opp(k) exchanged (half-way
-// bounce-back).
+// Slot population k of node self is read from / written to in each streaming mode. Across a
+// wall both fall back to the node itself with k and opp(k) exchanged (half-way bounce-back).
 template <int MODE>
-__device__ __forceinline__ Slot src_slot(int k, int ex, int ey, int ez, const Nbr& nb, int self) {
-    if (MODE == AA_EVEN || k == 0) return {self, k};
-    int q;
-    const bool in = nb.at(-ex, -ey, -ez, self, q);
-    if (MODE == AA_ODD) return in ? Slot{q, opp(k)} : Slot{self, k};
-    return in ? Slot{q, k} : Slot{self, opp(k)};
-}
-template <int MODE>
-__device__ __forceinline__ Slot dst_slot(int k, int ex, int ey, int ez, const Nbr& nb, int self) {
-    if (k == 0 || MODE == PULL) return {self, k};
-    if (MODE == AA_EVEN) return {self, opp(k)};
-    int q;
-    return nb.at(ex, ey, ez, self, q) ? Slot{q, k} : Slot{self, opp(k)};
-}
-
-// Addressing of one node's populations through its wrapped neighbour table (branch-free
-// selects, so warps straddling a domain edge do not diverge): the slot population k is read
-// from (src) and written to (dst), and phi of a neighbour in a phi array (mirror ghost
-// across walls).
-template <int MODE>
-struct AddrWrap {
+struct Addr {
     Nbr nb;
     int self;
-    __device__ __forceinline__ Slot src(int k, int ex, int ey, int ez) const { return src_slot<MODE>(k, ex, ey, ez, nb, self); }
-    __device__ __forceinline__ Slot dst(int k, int ex, int ey, int ez) const { return dst_slot<MODE>(k, ex, ey, ez, nb, self); }
+    __device__ __forceinline__ Slot src(int k, int ex, int ey, int ez) const {
+        if (MODE == AA_EVEN || k == 0) return {self, k};
+        int q;
+        const bool in = nb.at(-ex, -ey, -ez, self, q);
+        if (MODE == AA_ODD) return in ? Slot{q, opp(k)} : Slot{self, k};
+        return in ? Slot{q, k} : Slot{self, opp(k)};
+    }
+    __device__ __forceinline__ Slot dst(int k, int ex, int ey, int ez) const {
+        if (k == 0 || MODE == PULL) return {self, k};
+        if (MODE == AA_EVEN) return {self, opp(k)};
+        int q;
+        return nb.at(ex, ey, ez, self, q) ? Slot{q, k} : Slot{self, opp(k)};
+    }
+    // phi of a neighbour in a phi array, mirror ghost across walls (zero normal gradient)
     template <class R>
-    __device__ __forceinline__ R phi(const R* __restrict__ f, int dx, int dy, int dz) const;
+    __device__ __forceinline__ R phi(const R* __restrict__ f, int dx, int dy, int dz) const {
+        const int xx = nb.c[0][dx + 1] >= 0 ? nb.c[0][dx + 1] : nb.c[0][1];
+        const int r = nb.c[2][dz + 1] >= 0 ? nb.row[dz + 1][dy + 1] : nb.row[1][dy + 1];
+        return f[r + xx];
+    }
 };
 
 // Incoming populations of one node and their moments (steps a1-a3 of one node).
@@ -99,36 +99,29 @@ struct Node {
     R f[FLOW ? 19 : 1];
     R phit, dcA, dcB, S;
 
-    template <class Addr>
-    __device__ __forceinline__ void gather_scalars(const StateView& st, const Addr& ad, const DevParams& P) {
-        const T* G = static_cast<const T*>(st.g);
-        const T* HA = static_cast<const T*>(st.hA);
-        const T* HB = static_cast<const T*>(st.hB);
-        const float* rg = st.rest;
-        const float* ra = st.rest ? st.rest + P.plane : nullptr;
-        const float* rb = st.rest ? st.rest + 2 * P.plane : nullptr;
+    template <class A>
+    __device__ __forceinline__ void gather_scalars(const StateView& st, const A& ad, const DevParams& P) {
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
             const Slot s = ad.src(k, Scalar<LAT>::ex(k), Scalar<LAT>::ey(k), Scalar<LAT>::ez(k));
-            g[k] = load_scalar<T, SET_G, LAT>(G, rg, k, s, P);
-            hA[k] = load_scalar<T, SET_H, LAT>(HA, ra, k, s, P);
-            hB[k] = load_scalar<T, SET_H, LAT>(HB, rb, k, s, P);
+            g[k] = load_scalar<T, SET_G, LAT, kPlaneG, 0>(st, k, s, P);
+            hA[k] = load_scalar<T, SET_H, LAT, kPlaneHA, 1>(st, k, s, P);
+            hB[k] = load_scalar<T, SET_H, LAT, kPlaneHB, 2>(st, k, s, P);
         }
     }
-    template <class Addr>
-    __device__ __forceinline__ void gather_flow(const StateView& st, const Addr& ad, const DevParams& P) {
+    template <class A>
+    __device__ __forceinline__ void gather_flow(const StateView& st, const A& ad, const DevParams& P) {
         if constexpr (FLOW) {
-            const T* F = static_cast<const T*>(st.f);
 #pragma unroll
             for (int k = 0; k < 19; ++k) {
                 const Slot s = ad.src(k, D3Q19::ex(k), D3Q19::ey(k), D3Q19::ez(k));
                 if (is16<T>() && k == 0) f[0] = st.rest[3 * P.plane + s.node];
-                else f[k] = Codec<T>::template load<SET_F>(F + (long long)s.slot * P.plane + s.node, D3Q19::w(k), P);
+                else f[k] = Codec<T>::template load<SET_F>(element<T, 0>(st, k, s), D3Q19::w(k), P);
             }
         }
     }
-    template <class Addr>
-    __device__ __forceinline__ void gather(const StateView& st, const Addr& ad, const DevParams& P) {
+    template <class A>
+    __device__ __forceinline__ void gather(const StateView& st, const A& ad, const DevParams& P) {
         gather_scalars(st, ad, P);
         gather_flow(st, ad, P);
     }
@@ -145,21 +138,6 @@ struct Node {
     __device__ __forceinline__ R cA(const DevParams& P) const { return dcA + R(P.c0[0]); }
     __device__ __forceinline__ R cB(const DevParams& P) const { return dcB + R(P.c0[1]); }
 };
-
-// phi at x + e from a phi array: periodic wrap, mirror ghost across walls (zero normal gradient).
-template <class R>
-__device__ __forceinline__ R phi_at(const R* __restrict__ phi, const Nbr& nb, int dx, int dy, int dz) {
-    // both candidates are indexed with constants (dx, dy, dz are unrolled), so Nbr stays in registers
-    const int xx = nb.c[0][dx + 1] >= 0 ? nb.c[0][dx + 1] : nb.c[0][1];
-    const int r = nb.c[2][dz + 1] >= 0 ? nb.row[dz + 1][dy + 1] : nb.row[1][dy + 1];
-    return phi[r + xx];
-}
-
-template <int MODE>
-template <class R>
-__device__ __forceinline__ R AddrWrap<MODE>::phi(const R* __restrict__ f, int dx, int dy, int dz) const {
-    return phi_at(f, nb, dx, dy, dz);
-}
 
 // Eqs. 42-45 regrouped over opposite pairs: grad = 3 sum_k w_k e_k phi(x+e_k),
 // lap = 6 sum_k w_k (phi(x+e_k) - phi(x)), k = 1..18 of D3Q19. ``get(dx, dy, dz)`` returns
@@ -203,87 +181,95 @@ __device__ __forceinline__ void force_velocity(const R* f, R phi, R gx, R gy, R 
 __device__ __forceinline__ float recip(float v) { return __frcp_rn(v); }
 __device__ __forceinline__ double recip(double v) { return 1.0 / v; }
 
+// e . v for a lattice vector with components in {-1, 0, 1}, without multiplications
+template <class R>
+__device__ __forceinline__ R edot(int ex, int ey, int ez, R vx, R vy, R vz) {
+    R s = R(0);
+    if (ex) s = ex > 0 ? vx : -vx;
+    if (ey) s = ey > 0 ? s + vy : s - vy;
+    if (ez) s = ez > 0 ? s + vz : s - vz;
+    return s;
+}
+
 // Collisions of one node (steps a6-a8) and the scatter of the post-collision values.
-template <class T, int LAT, bool FLOW, class Addr>
+// Each BGK update keeps the form P* = P - om (P - P^eq) (+ source), which rounds only the
+// small non-equilibrium difference; the equilibria reuse node-wide terms:
+//   f:  Gamma_k = w (A + cu (3 + 4.5 cu)), A = 1 - 1.5 u^2; F_k = Gamma_k (e.F - u.F);
+//       f^eq = w (B + cu (1 + 1.5 cu)) - F_k / 2, B = p_h - 0.5 u^2          (Eqs. 36-39)
+//   g:  g^eq = w (phi - S/2 + phi cu / cs2), g* = g - om (g - g^eq) + w S    (Eqs. 46-48)
+//   h:  h^eq_k = w (mu + c cu / cs2), h^eq_0 = dc - (1 - w_0) mu (shifted)   (Eqs. 50-51)
+template <class T, int LAT, bool FLOW, class A>
 __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, typename RealOf<T>::type phi,
                                               typename RealOf<T>::type ux, typename RealOf<T>::type uy,
                                               typename RealOf<T>::type uz, typename RealOf<T>::type Fx,
                                               typename RealOf<T>::type Fy, typename RealOf<T>::type Fz,
-                                              const StateView& out, const Addr& ad, const DevParams& P) {
-    const int self = ad.self;
+                                              const StateView& out, const A& ad, const DevParams& P) {
     using R = typename RealOf<T>::type;
     using L = Scalar<LAT>;
     constexpr int Q = L::Q;
+    const int self = ad.self;
     if constexpr (FLOW) {
-        // Eqs. 36-39: He-Shan-Doolen forcing, He-Luo equilibrium shifted by -F_k/2
         R ph = R(0);
 #pragma unroll
         for (int k = 0; k < 19; ++k) ph += nd.f[k];
         const R usq = ux * ux + uy * uy + uz * uz;
+        const R Ac = R(1) - R(1.5) * usq;
+        const R Bc = ph - R(0.5) * usq;
+        const R uF = ux * Fx + uy * Fy + uz * Fz;
         const R omf = R(P.om_f);
-        T* F = static_cast<T*>(out.f);
         R f0post = R(0), resid = R(0);
 #pragma unroll
         for (int k = 0; k < 19; ++k) {
+            const int ex = D3Q19::ex(k), ey = D3Q19::ey(k), ez = D3Q19::ez(k);
             const R w = R(D3Q19::w(k));
-            const R cu = R(D3Q19::ex(k)) * ux + R(D3Q19::ey(k)) * uy + R(D3Q19::ez(k)) * uz;
-            const R gam = w * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * usq);
-            const R Fk = gam * ((R(D3Q19::ex(k)) - ux) * Fx + (R(D3Q19::ey(k)) - uy) * Fy + (R(D3Q19::ez(k)) - uz) * Fz);
-            const R feq = w * (ph + cu + R(1.5) * cu * cu - R(0.5) * usq) - R(0.5) * Fk;
+            const R cu = edot(ex, ey, ez, ux, uy, uz);
+            const R Fk = w * (Ac + cu * (R(3) + R(4.5) * cu)) * (edot(ex, ey, ez, Fx, Fy, Fz) - uF);
+            const R feq = w * (Bc + cu * (R(1) + R(1.5) * cu)) - R(0.5) * Fk;
             const R post = nd.f[k] - omf * (nd.f[k] - feq) + Fk;
-            const Slot s = ad.dst(k, D3Q19::ex(k), D3Q19::ey(k), D3Q19::ez(k));
             if (is16<T>() && k == 0) { f0post = post; continue; }
-            resid += Codec<T>::template store_residual<SET_F>(F + (long long)s.slot * P.plane + s.node, post,
-                                                              D3Q19::w(k), P);
+            const Slot s = ad.dst(k, ex, ey, ez);
+            resid += Codec<T>::template store_residual<SET_F>(element<T, 0>(out, k, s), post, D3Q19::w(k), P);
         }
         if (is16<T>()) out.rest[3 * P.plane + self] = float(f0post + resid);
     }
-    const R S = nd.S;
     const R p = interp_p(phi);
     const R muA = closure_dev(nd.dcA, p, 0, P);
     const R muB = closure_dev(nd.dcB, p, 1, P);
     const R inv_cs2 = R(L::cs2() == 0.25 ? 4.0 : 3.0);
     const R omg = R(P.om_g);
-    // Eqs. 50-51 with M^alpha(phi) of §2.3 and tau_h = M / c_s^2
-    const R MA = R(P.M0[0]) * (R(1) - phi) + R(P.M1[0]) * phi;
+    const R MA = R(P.M0[0]) * (R(1) - phi) + R(P.M1[0]) * phi;     // §2.3
     const R MB = R(P.M0[1]) * (R(1) - phi) + R(P.M1[1]) * phi;
-    const R omA = recip(MA * inv_cs2 + R(0.5));
+    const R omA = recip(MA * inv_cs2 + R(0.5));                      // tau_h = M / c_s^2
     const R omB = recip(MB * inv_cs2 + R(0.5));
-    T* G = static_cast<T*>(out.g);
-    T* HA = static_cast<T*>(out.hA);
-    T* HB = static_cast<T*>(out.hB);
-    float* rg = out.rest;
-    float* ra = out.rest ? out.rest + P.plane : nullptr;
-    float* rb = out.rest ? out.rest + 2 * P.plane : nullptr;
-    R g0 = R(0), hA0 = R(0), hB0 = R(0);          // rest populations, stored last
+    const R ga = phi - R(0.5) * nd.S;                                 // g^eq = w (ga + gb cu)
+    const R gb = phi * inv_cs2;
+    const R cAu = nd.cA(P) * inv_cs2, cBu = nd.cB(P) * inv_cs2;
+    R g0 = R(0), hA0 = R(0), hB0 = R(0);                              // rest populations, stored last
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
+        const int ex = L::ex(k), ey = L::ey(k), ez = L::ez(k);
         const R w = R(L::w(k));
-        const R cu = R(L::ex(k)) * ux + R(L::ey(k)) * uy + R(L::ez(k)) * uz;
-        // Eqs. 46-48
-        const R geq = w * phi * (R(1) + inv_cs2 * cu) - R(0.5) * w * S;
-        const R gpost = nd.g[k] - omg * (nd.g[k] - geq) + w * S;
-        R heqA, heqB;
-        if (k == 0) {                      // shifted by c_0^eq like the stored h_0
-            heqA = nd.dcA - (R(1) - w) * muA;
-            heqB = nd.dcB - (R(1) - w) * muB;
-        } else {
-            heqA = w * muA + w * nd.cA(P) * inv_cs2 * cu;
-            heqB = w * muB + w * nd.cB(P) * inv_cs2 * cu;
+        const R cu = edot(ex, ey, ez, ux, uy, uz);
+        const R geq = w * (ga + gb * cu);
+        const R gpost = nd.g[k] - omg * (nd.g[k] - geq) + w * nd.S;
+        if (k == 0) {                                                 // h_0 shifted by c_0^eq
+            g0 = gpost;
+            hA0 = nd.hA[0] - omA * (nd.hA[0] - (nd.dcA - (R(1) - w) * muA));
+            hB0 = nd.hB[0] - omB * (nd.hB[0] - (nd.dcB - (R(1) - w) * muB));
+            continue;
         }
-        const R hApost = nd.hA[k] - omA * (nd.hA[k] - heqA);
-        const R hBpost = nd.hB[k] - omB * (nd.hB[k] - heqB);
-        if (k == 0) { g0 = gpost; hA0 = hApost; hB0 = hBpost; continue; }
-        const Slot s = ad.dst(k, L::ex(k), L::ey(k), L::ez(k));
+        const R hApost = nd.hA[k] - omA * (nd.hA[k] - w * (muA + cAu * cu));
+        const R hBpost = nd.hB[k] - omB * (nd.hB[k] - w * (muB + cBu * cu));
+        const Slot s = ad.dst(k, ex, ey, ez);
         // 16-bit storage: rounding residuals of the moving populations go to the rest population
-        g0 += store_moving<T, SET_G, LAT>(G, k, s, gpost, P);
-        hA0 += store_moving<T, SET_H, LAT>(HA, k, s, hApost, P);
-        hB0 += store_moving<T, SET_H, LAT>(HB, k, s, hBpost, P);
+        g0 += store_moving<T, SET_G, LAT, kPlaneG>(out, k, s, gpost, P);
+        hA0 += store_moving<T, SET_H, LAT, kPlaneHA>(out, k, s, hApost, P);
+        hB0 += store_moving<T, SET_H, LAT, kPlaneHB>(out, k, s, hBpost, P);
     }
     const Slot s0{self, 0};
-    store_scalar<T, SET_G, LAT>(G, rg, 0, s0, g0, P);
-    store_scalar<T, SET_H, LAT>(HA, ra, 0, s0, hA0, P);
-    store_scalar<T, SET_H, LAT>(HB, rb, 0, s0, hB0, P);
+    store_scalar<T, SET_G, LAT, kPlaneG, 0>(out, 0, s0, g0, P);
+    store_scalar<T, SET_H, LAT, kPlaneHA, 1>(out, 0, s0, hA0, P);
+    store_scalar<T, SET_H, LAT, kPlaneHB, 2>(out, 0, s0, hB0, P);
 }
 
 // ------------------------------------------------------------------------------------
@@ -297,15 +283,14 @@ step_kernel(const DevParams P, const StateView st, const StateView out,
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     if (x >= P.nx) return;
-    const int self = node_of(x, y, z, P);
-    AddrWrap<MODE> ad;
-    ad.self = self;
+    Addr<MODE> ad;
+    ad.self = node_of(x, y, z, P);
     ad.nb.init(x, y, z, P);
     Node<T, LAT, FLOW> nd;
     nd.gather(st, ad, P);
     nd.moments(P);
     R phi;
-    if constexpr (FLOW) phi = phi_field[self]; else phi = nd.phi();
+    if constexpr (FLOW) phi = phi_field[ad.self]; else phi = nd.phi();
     R ux = R(0), uy = R(0), uz = R(0), Fx = R(0), Fy = R(0), Fz = R(0);
     if constexpr (FLOW) {
         R gx, gy, gz, lap;
@@ -322,14 +307,13 @@ phi_kernel(const DevParams P, const StateView st, typename RealOf<T>::type* __re
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     if (x >= P.nx) return;
-    const int self = node_of(x, y, z, P);
-    AddrWrap<MODE> ad;
-    ad.self = self;
+    Addr<MODE> ad;
+    ad.self = node_of(x, y, z, P);
     ad.nb.init(x, y, z, P);
     Node<T, LAT, false> nd;
     nd.gather_scalars(st, ad, P);
     nd.moments(P);
-    phi_out[self] = nd.phi();
+    phi_out[ad.self] = nd.phi();
 }
 
 // ------------------------------------------------------------------------------------
@@ -348,8 +332,9 @@ constexpr int FX = 32, FY = 8, FT = FX * FY;
 constexpr int kHalo = 2 * (FX + 2) + 2 * FY;    // ring positions outside the tile (84)
 constexpr int kSPops = 3 * 7 + 3;               // 21 scalar populations + S, dcA, dcB
 
-template <class R>
+template <class T>
 __host__ __device__ constexpr size_t fused_smem_bytes() {
+    using R = typename RealOf<T>::type;
     return sizeof(R) * (3 * (FY + 2) * (FX + 2) + 2 * kSPops * FT);
 }
 
@@ -370,7 +355,7 @@ fused_flow_kernel(const DevParams P, const StateView src, const StateView dst, i
     const int x = x0 + tx, y = y0 + ty;
     const bool active = x < P.nx && y < P.ny;
 
-    // domain position of ring position (hx, hy): periodic wrap in x and y, mirror across x walls
+    // domain column of ring position (hx, hy): periodic wrap in x and y, mirror across x walls
     auto wrap_xy = [&](int hx, int hy, int& gx, int& gy) {
         gx = x0 + hx;
         gy = y0 + hy;
@@ -385,53 +370,57 @@ fused_flow_kernel(const DevParams P, const StateView src, const StateView dst, i
         if (zz >= P.nz) return P.wall_z ? P.nz - 1 : zz - P.nz;
         return zz;
     };
+    // this thread's own ring column and its halo column (threads tid < kHalo), fixed in z
+    int ox, oy, hxp = 0, hyp = 0, hgx = 0, hgy = 0;
+    const bool own_ok = wrap_xy(tx, ty, ox, oy);
+    bool halo_ok = false;
+    if (tid < kHalo) {
+        if (tid < FX + 2) { hxp = tid - 1; hyp = -1; }
+        else if (tid < 2 * (FX + 2)) { hxp = tid - (FX + 2) - 1; hyp = FY; }
+        else if (tid < 2 * (FX + 2) + FY) { hxp = -1; hyp = tid - 2 * (FX + 2); }
+        else { hxp = FX; hyp = tid - 2 * (FX + 2) - FY; }
+        halo_ok = wrap_xy(hxp, hyp, hgx, hgy);
+    }
+    Addr<PULL> own, halo;
+    own.nb.init_xy(ox, oy, P);
+    halo.nb.init_xy(hgx, hgy, P);
+
     // phi (and, for a tile node, its scalar populations in buffer buf) of plane zz
     auto fill = [&](int zz, int s, int buf) {
         const int zr = zwrap(zz);
-        {
-            int gx, gy;
-            R v = R(0);
-            if (wrap_xy(tx, ty, gx, gy)) {
-                AddrWrap<PULL> ad;
-                ad.self = node_of(gx, gy, zr, P);
-                ad.nb.init(gx, gy, zr, P);
-                Node<T, LAT_D3Q7, false> nd;
-                nd.gather_scalars(src, ad, P);
-                nd.moments(P);
-                v = nd.phi();
-                if (active && buf >= 0) {
-                    R* sp = spops + buf * kSPops * FT + tid;
+        R v = R(0);
+        if (own_ok) {
+            own.self = node_of(ox, oy, zr, P);
+            own.nb.set_z(zr, P);
+            Node<T, LAT_D3Q7, false> nd;
+            nd.gather_scalars(src, own, P);
+            nd.moments(P);
+            v = nd.phi();
+            if (active && buf >= 0) {
+                R* sp = spops + buf * kSPops * FT + tid;
 #pragma unroll
-                    for (int k = 0; k < Q; ++k) {
-                        sp[k * FT] = nd.g[k];
-                        sp[(Q + k) * FT] = nd.hA[k];
-                        sp[(2 * Q + k) * FT] = nd.hB[k];
-                    }
-                    sp[(3 * Q) * FT] = nd.S;
-                    sp[(3 * Q + 1) * FT] = nd.dcA;
-                    sp[(3 * Q + 2) * FT] = nd.dcB;
+                for (int k = 0; k < Q; ++k) {
+                    sp[k * FT] = nd.g[k];
+                    sp[(Q + k) * FT] = nd.hA[k];
+                    sp[(2 * Q + k) * FT] = nd.hB[k];
                 }
+                sp[(3 * Q) * FT] = nd.S;
+                sp[(3 * Q + 1) * FT] = nd.dcA;
+                sp[(3 * Q + 2) * FT] = nd.dcB;
             }
-            ring[s][ty + 1][tx + 1] = v;
         }
+        ring[s][ty + 1][tx + 1] = v;
         if (tid < kHalo) {
-            int hx, hy;
-            if (tid < FX + 2) { hx = tid - 1; hy = -1; }
-            else if (tid < 2 * (FX + 2)) { hx = tid - (FX + 2) - 1; hy = FY; }
-            else if (tid < 2 * (FX + 2) + FY) { hx = -1; hy = tid - 2 * (FX + 2); }
-            else { hx = FX; hy = tid - 2 * (FX + 2) - FY; }
-            int gx, gy;
-            R v = R(0);
-            if (wrap_xy(hx, hy, gx, gy)) {
-                AddrWrap<PULL> ad;
-                ad.self = node_of(gx, gy, zr, P);
-                ad.nb.init(gx, gy, zr, P);
+            R hv = R(0);
+            if (halo_ok) {
+                halo.self = node_of(hgx, hgy, zr, P);
+                halo.nb.set_z(zr, P);
                 Node<T, LAT_D3Q7, false> nd;
-                nd.gather_scalars(src, ad, P);
+                nd.gather_scalars(src, halo, P);
                 nd.moments(P);
-                v = nd.phi();
+                hv = nd.phi();
             }
-            ring[s][hy + 1][hx + 1] = v;
+            ring[s][hyp + 1][hxp + 1] = hv;
         }
     };
 
@@ -442,11 +431,10 @@ fused_flow_kernel(const DevParams P, const StateView src, const StateView dst, i
         fill(z + 1, sn, (z + 1) & 1);
         __syncthreads();
         if (active) {
-            AddrWrap<PULL> ad;
-            ad.self = node_of(x, y, z, P);
-            ad.nb.init(x, y, z, P);
+            own.self = node_of(x, y, z, P);
+            own.nb.set_z(z, P);
             Node<T, LAT_D3Q7, true> nd;
-            nd.gather_flow(src, ad, P);
+            nd.gather_flow(src, own, P);
             const R* spc = spops + (z & 1) * kSPops * FT + tid;
             nd.S = spc[(3 * Q) * FT];
             nd.dcA = spc[(3 * Q + 1) * FT];
@@ -464,7 +452,7 @@ fused_flow_kernel(const DevParams P, const StateView src, const StateView dst, i
                         return ring[s][ty + 1 + dy][tx + 1 + dx];
                     }, phi, gx, gy, gz, lap);
             force_velocity(nd.f, phi, gx, gy, gz, lap, P, Fx, Fy, Fz, ux, uy, uz);
-            collide_store(nd, phi, ux, uy, uz, Fx, Fy, Fz, dst, ad, P);
+            collide_store(nd, phi, ux, uy, uz, Fx, Fy, Fz, dst, own, P);
         }
         __syncthreads();
         const int t = sp; sp = sc; sc = sn; sn = t;
@@ -479,13 +467,14 @@ fused_flow_kernel(const DevParams P, const StateView src, const StateView dst, i
 enum { INIT_G = 0, INIT_HA = 1, INIT_HB = 2, INIT_F = 3 };
 
 template <int LAT>
-__device__ __forceinline__ double init_value(int set, int k, int node, const Nbr& nb,
+__device__ __forceinline__ double init_value(int set, int k, const Addr<PULL>& ad,
                                              const double* __restrict__ phi0, const double* __restrict__ cA0,
                                              const double* __restrict__ cB0, const DevParams& P) {
+    const int node = ad.self;
     const double ph = phi0[node];
     if (set == INIT_F) {
         double gx, gy, gz, lap;
-        stencil([&](int dx, int dy, int dz) { return phi_at(phi0, nb, dx, dy, dz); }, ph, gx, gy, gz, lap);
+        stencil([&](int dx, int dy, int dz) { return ad.phi(phi0, dx, dy, dz); }, ph, gx, gy, gz, lap);
         const double br = P.sw15 * (dwell_d(ph) * P.inv_W2 - lap);
         const double Fx = br * gx + ph * P.g[0], Fy = br * gy + ph * P.g[1], Fz = br * gz + ph * P.g[2];
         const double w = D3Q19::w(k);
@@ -512,20 +501,16 @@ init_kernel(const DevParams P, const StateView st, const double* __restrict__ ph
     const int self = node_of(x, y, z, P);
     Nbr nb;
     nb.init(x, y, z, P);
-    T* G = static_cast<T*>(st.g);
-    T* HA = static_cast<T*>(st.hA);
-    T* HB = static_cast<T*>(st.hB);
-    float* rg = st.rest;
-    float* ra = st.rest ? st.rest + P.plane : nullptr;
-    float* rb = st.rest ? st.rest + 2 * P.plane : nullptr;
     // which node's initial population (and which index) slot k of this node holds
-    auto source_of = [&](int k, int ex, int ey, int ez, int& node, int& kk, Nbr& snb) {
-        node = self; kk = k; snb = nb;
+    auto source_of = [&](int k, int ex, int ey, int ez, int& kk, Addr<PULL>& sad) {
+        sad.nb = nb;
+        sad.self = self;
+        kk = k;
         if (MODE == PULL && k != 0) {
             int q;
             if (nb.at(ex, ey, ez, self, q)) {
-                node = q;
-                snb.init(nb.c[0][ex + 1], nb.c[1][ey + 1], nb.c[2][ez + 1], P);
+                sad.self = q;
+                sad.nb.init(nb.c[0][ex + 1], nb.c[1][ey + 1], nb.c[2][ez + 1], P);
             } else {
                 kk = opp(k);
             }
@@ -533,22 +518,23 @@ init_kernel(const DevParams P, const StateView st, const double* __restrict__ ph
     };
 #pragma unroll 1
     for (int k = 0; k < L::Q; ++k) {
-        int node; int kk; Nbr snb;
-        source_of(k, L::ex(k), L::ey(k), L::ez(k), node, kk, snb);
+        int kk;
+        Addr<PULL> sad;
+        source_of(k, L::ex(k), L::ey(k), L::ez(k), kk, sad);
         const Slot s{self, k};
-        store_scalar<T, SET_G, LAT>(G, rg, k, s, R(init_value<LAT>(INIT_G, kk, node, snb, phi0, cA0, cB0, P)), P);
-        store_scalar<T, SET_H, LAT>(HA, ra, k, s, R(init_value<LAT>(INIT_HA, kk, node, snb, phi0, cA0, cB0, P)), P);
-        store_scalar<T, SET_H, LAT>(HB, rb, k, s, R(init_value<LAT>(INIT_HB, kk, node, snb, phi0, cA0, cB0, P)), P);
+        store_scalar<T, SET_G, LAT, kPlaneG, 0>(st, k, s, R(init_value<LAT>(INIT_G, kk, sad, phi0, cA0, cB0, P)), P);
+        store_scalar<T, SET_H, LAT, kPlaneHA, 1>(st, k, s, R(init_value<LAT>(INIT_HA, kk, sad, phi0, cA0, cB0, P)), P);
+        store_scalar<T, SET_H, LAT, kPlaneHB, 2>(st, k, s, R(init_value<LAT>(INIT_HB, kk, sad, phi0, cA0, cB0, P)), P);
     }
     if constexpr (FLOW) {
-        T* F = static_cast<T*>(st.f);
 #pragma unroll 1
         for (int k = 0; k < 19; ++k) {
-            int node; int kk; Nbr snb;
-            source_of(k, D3Q19::ex(k), D3Q19::ey(k), D3Q19::ez(k), node, kk, snb);
-            const R v = R(init_value<LAT>(INIT_F, kk, node, snb, phi0, cA0, cB0, P));
+            int kk;
+            Addr<PULL> sad;
+            source_of(k, D3Q19::ex(k), D3Q19::ey(k), D3Q19::ez(k), kk, sad);
+            const R v = R(init_value<LAT>(INIT_F, kk, sad, phi0, cA0, cB0, P));
             if (is16<T>() && k == 0) st.rest[3 * P.plane + self] = float(v);
-            else Codec<T>::template store<SET_F>(F + (long long)k * P.plane + self, v, D3Q19::w(k), P);
+            else Codec<T>::template store<SET_F>(element<T, 0>(st, k, Slot{self, k}), v, D3Q19::w(k), P);
         }
     }
 }
@@ -562,15 +548,14 @@ fields_kernel(const DevParams P, const StateView st, const typename RealOf<T>::t
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     if (x >= P.nx) return;
-    const int self = node_of(x, y, z, P);
-    AddrWrap<MODE> ad;
+    Addr<MODE> ad;
+    ad.self = node_of(x, y, z, P);
     ad.nb.init(x, y, z, P);
-    ad.self = self;
     Node<T, LAT, FLOW> nd;
     nd.gather(st, ad, P);
     nd.moments(P);
     R phi;
-    if constexpr (FLOW) phi = phi_field[self]; else phi = nd.phi();
+    if constexpr (FLOW) phi = phi_field[ad.self]; else phi = nd.phi();
     const R p = interp_p(phi);
     R vals[LBM_NFIELDS_DEV];
     vals[0] = phi;
@@ -591,7 +576,7 @@ fields_kernel(const DevParams P, const StateView st, const typename RealOf<T>::t
     }
 #pragma unroll
     for (int i = 0; i < LBM_NFIELDS_DEV; ++i)
-        if (out.p[i]) static_cast<R*>(out.p[i])[self] = vals[i];
+        if (out.p[i]) static_cast<R*>(out.p[i])[ad.self] = vals[i];
 }
 
 // FP64 block partials of the global diagnostics (grid-stride over nodes).
@@ -608,9 +593,9 @@ reduce_kernel(const DevParams P, const StateView st, const typename RealOf<T>::t
         const int x = int(id % P.nx);
         const int y = int((id / P.nx) % P.ny);
         const int z = int(id / ((long long)P.nx * P.ny));
-        AddrWrap<MODE> ad;
-        ad.nb.init(x, y, z, P);
+        Addr<MODE> ad;
         ad.self = int(id);
+        ad.nb.init(x, y, z, P);
         Node<T, LAT, FLOW> nd;
         nd.gather(st, ad, P);
         nd.moments(P);
@@ -707,7 +692,7 @@ struct Launchers {
     static void fused(const DevParams& P, const StateView& src, const StateView& dst, int zchunk, cudaStream_t s) {
         const dim3 block(FX, FY);
         const dim3 grid((P.nx + FX - 1) / FX, (P.ny + FY - 1) / FY, (P.nz + zchunk - 1) / zchunk);
-        constexpr size_t smem = fused_smem_bytes<R>();
+        constexpr size_t smem = fused_smem_bytes<T>();
         // opt in to more than 48 KB of dynamic shared memory, once per device (a repeated
         // call from a racing thread is harmless)
         static unsigned long long configured = 0;
