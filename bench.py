@@ -28,6 +28,10 @@ N = 512
 # bytes each node reads and writes per step: 40 populations; 16-bit storage keeps the
 # four rest populations g_0, h^A_0, h^B_0, f_0 in FP32 (36 x 2 B + 4 x 4 B = 88 B each way)
 ALG_BYTES_PER_NODE = {"f32": 320.0, "f16": 176.0, "bf16": 176.0, "f64": 640.0}
+# DRAM bytes (read + write) per node of one fused_flow_kernel<float> launch, from an ncu capture
+# of this kernel at 192^3 (profiles/fused_flow_kernel_f32_192cube.md); traffic scales with the
+# node count. Set to None whenever the kernel changes until it is captured again.
+NCU_DRAM_BYTES_PER_NODE_F32 = 163.18 + 153.65
 
 
 def parse():
@@ -179,28 +183,29 @@ def time_adjoint(device, n=128, steps=200, K=100):
     p, fields = configs.adjoint_problem(n=n)
     phi0, cA0, cB0 = fields(device=device)
     target = forward_fields(p, configs.THETA_TARGET, phi0, cA0, cB0, steps, device=device)
-    forward_fields(p, configs.THETA_EVAL, phi0, cA0, cB0, 10, device=device)   # warm-up
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    forward_fields(p, configs.THETA_EVAL, phi0, cA0, cB0, steps, device=device)
-    torch.cuda.synchronize()
-    fwd = time.perf_counter() - t0
-    th = torch.tensor(configs.THETA_EVAL, dtype=torch.float64, requires_grad=True)
-    p0 = phi0.clone().requires_grad_(True)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    out = CoupledRun.apply(p0, th, p, cA0, cB0, steps, K)
-    L = misfit(out, target)
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    L.backward()
-    torch.cuda.synchronize()
-    t2 = time.perf_counter()
+
+    def run():
+        th = torch.tensor(configs.THETA_EVAL, dtype=torch.float64, requires_grad=True)
+        p0 = phi0.clone().requires_grad_(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = CoupledRun.apply(p0, th, p, cA0, cB0, steps, K)
+        L = misfit(out, target)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        L.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        return t1 - t0, t2 - t1, th
+
+    run()                                            # warm-up (module loading, allocator)
+    fwd, bwd, th = run()
     return {"workload": f"{n}^3 ripening, FP32, {steps} steps, checkpoint every {K}",
             "forward_ms_per_step": fwd / steps * 1e3,
-            "checkpointed_forward_ms_per_step": (t1 - t0) / steps * 1e3,
-            "backward_ms_per_step": (t2 - t1) / steps * 1e3,
-            "backward_over_forward": (t2 - t1) / fwd,
+            "backward_ms_per_step": bwd / steps * 1e3,
+            "backward_over_forward": bwd / fwd,
+            "timing": "wall clock around CoupledRun.apply + misfit (forward, with checkpoints) and "
+                      "L.backward() (recompute from checkpoints + adjoint sweep), synchronised, after one warm-up run",
             "alg_bytes_per_node": {"forward": 168, "recompute": 168, "adjoint_step": 252},
             "grad_theta": [float(v) for v in th.grad]}
 
@@ -262,7 +267,8 @@ def gb300(args):
                    "lattice": [p.nx, p.ny, p.nz], "storage": "f32",
                    "l2": "state 21.5 GB >> 129 MB L2, no flush", "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": None if NCU_DRAM_BYTES_PER_NODE_F32 is None else NCU_DRAM_BYTES_PER_NODE_F32 * nodes,
                      "kernel": "fused_flow_kernel<float> (z-marching fused phi + collide + stream)",
                      "alg_bytes_per_launch": bytes_step, "ms_per_launch": ms_step,
                      "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
