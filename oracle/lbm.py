@@ -94,15 +94,28 @@ class OracleLBM:
         return torch.stack(moved)
 
     def _neighbour(self, phi, e):
-        """phi(x + e): periodic in x and y, mirror ghost across the z walls (§4.2.4)."""
+        """phi(x + e): periodic on open axes; across a wall (z walls of §4.2.4, x walls of the
+        couple geometry) the mirror ghost, i.e. the walled component of e is dropped."""
         ex, ey, ez = e
-        out = torch.roll(phi, shifts=(-ez, -ey, -ex), dims=(0, 1, 2))
+        nz, ny, nx = self.p.shape
+        beyond_z = beyond_x = None
         if self.p.wall_z and ez != 0:
-            nz = self.p.nz
             z = torch.arange(nz).reshape(-1, 1, 1)
-            beyond = ((z + ez < 0) | (z + ez >= nz)).expand(self.p.shape)
-            same_plane = torch.roll(phi, shifts=(0, -ey, -ex), dims=(0, 1, 2))
-            out = torch.where(beyond, same_plane, out)
+            beyond_z = ((z + ez < 0) | (z + ez >= nz)).expand(self.p.shape)
+        if self.p.wall_x and ex != 0:
+            x = torch.arange(nx).reshape(1, 1, -1)
+            beyond_x = ((x + ex < 0) | (x + ex >= nx)).expand(self.p.shape)
+
+        def rolled(dx, dz):
+            return torch.roll(phi, shifts=(-dz, -ey, -dx), dims=(0, 1, 2))
+
+        out = rolled(ex, ez)
+        if beyond_z is not None:
+            out = torch.where(beyond_z, rolled(ex, 0), out)
+        if beyond_x is not None:
+            out = torch.where(beyond_x, rolled(0, ez), out)
+        if beyond_z is not None and beyond_x is not None:
+            out = torch.where(beyond_z & beyond_x, rolled(0, 0), out)
         return out
 
     def gradient_laplacian(self, phi):

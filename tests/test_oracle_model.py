@@ -69,6 +69,36 @@ def test_derivatives_match_finite_differences():
     assert torch.allclose(m.p_interp(1 - x), 1 - m.p_interp(x), rtol=0, atol=1e-14)
 
 
+@pytest.mark.parametrize("axis", ["x", "z"])
+def test_stencil_mirror_ghost_at_walls(axis):
+    # phi = s^2 along the walled axis s only. On D3Q19 the stencil of Eqs. 42-45 reduces to
+    # grad_s = (phi(s+1) - phi(s-1)) / 2 and lap = phi(s+1) - 2 phi(s) + phi(s-1) (the weights
+    # with e_s = +1 sum to 1/6); the mirror ghost phi(-1) = phi(0) of a wall (zero normal
+    # gradient, §4.2.4) gives grad_s = 1/2 and lap = 1 at s = 0, and grad_s = -(2n - 3)/2,
+    # lap = -(2n - 3) at s = n - 1. A periodic wrap or a dropped mirror would differ.
+    n = 7
+    if axis == "x":
+        p = LBMParams(nx=n, ny=3, nz=4, lattice="D3Q7", flow=True, wall_x=True)
+        s = torch.arange(n, dtype=torch.float64).reshape(1, 1, -1).expand(p.shape)
+        a, pick = 0, (lambda f, i: f[:, :, i])
+    else:
+        p = LBMParams(nx=3, ny=4, nz=n, lattice="D3Q7", flow=True, wall_z=True)
+        s = torch.arange(n, dtype=torch.float64).reshape(-1, 1, 1).expand(p.shape)
+        a, pick = 2, (lambda f, i: f[i])
+    phi = (s * s).contiguous()
+    grad, lap = OracleLBM(p).gradient_laplacian(phi)
+    sv = torch.arange(n, dtype=torch.float64)
+    up = torch.cat([sv[1:], sv[-1:]]) ** 2            # phi(s + 1), mirrored at the top wall
+    dn = torch.cat([sv[:1], sv[:-1]]) ** 2            # phi(s - 1), mirrored at the bottom wall
+    for i in range(n):
+        assert torch.allclose(pick(grad[a], i), (up[i] - dn[i]) / 2 + 0 * pick(phi, i), rtol=0, atol=1e-13)
+        assert torch.allclose(pick(lap, i), up[i] - 2 * sv[i] ** 2 + dn[i] + 0 * pick(phi, i), rtol=0, atol=1e-13)
+    assert float(pick(grad[a], 0).max()) == 0.5 and float(pick(lap, 0).max()) == 1.0
+    for b in range(3):
+        if b != a:
+            assert float(grad[b].abs().max()) < 1e-13
+
+
 def test_tanh_profile_is_the_flat_equilibrium():
     # W^2 phi'' = omega_dw'(phi) for phi_0 of Eq. 13 (the interfacial part of the Allen-Cahn equation)
     W = 3.0
