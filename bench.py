@@ -31,7 +31,7 @@ ALG_BYTES_PER_NODE = {"f32": 320.0, "f16": 176.0, "bf16": 176.0, "f64": 640.0}
 # DRAM bytes (read + write) per node of one fused_flow_kernel<float> launch, from an ncu capture
 # of this kernel at 192^3 (profiles/fused_flow_kernel_f32_192cube.md); traffic scales with the
 # node count. Set to None whenever the kernel changes until it is captured again.
-NCU_DRAM_BYTES_PER_NODE_F32 = 163.18 + 153.65
+NCU_DRAM_BYTES_PER_NODE_F32 = None
 
 
 def parse():
@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--cpu-sample-planes", type=int, default=16)
     ap.add_argument("--cpu-sample-steps", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle leg (profiling runs)")
+    ap.add_argument("--adjoint-only", action="store_true", help="time only the adjoint variant (profiling runs)")
+    ap.add_argument("--adjoint-steps", type=int, default=200)
+    ap.add_argument("--adjoint-k", type=int, default=100, help="checkpoint interval of the adjoint variant")
     return ap.parse_args()
 
 
@@ -239,6 +242,11 @@ def run_e2e(p, init, steps, device):
 def gb300(args):
     import torch
     ws, rank, local = dist_env()
+    if args.adjoint_only:
+        torch.cuda.set_device(local)
+        print(json.dumps({"adjoint": time_adjoint(torch.device("cuda", local), steps=args.adjoint_steps,
+                                                  K=args.adjoint_k)}))
+        return
     dist = None
     if ws > 1:
         import torch.distributed as td
@@ -298,7 +306,7 @@ def gb300(args):
         out["variants"] = var
 
     if not args.no_variants:
-        out["variants"]["adjoint"] = time_adjoint(device)
+        out["variants"]["adjoint"] = time_adjoint(device, steps=args.adjoint_steps, K=args.adjoint_k)
 
     if not args.no_e2e:
         out["e2e"] = run_e2e(p, init, args.steps, device)

@@ -80,6 +80,23 @@ Layout layout_of(const lbm_params* p) {
     return L;
 }
 
+template <class R>
+void fill_coef(const DevParams& d, lbm::Coef<R>& c) {
+    c.lam = R(d.lam);
+    c.kphi = R(d.kphi);
+    for (int a = 0; a < 2; ++a) {
+        c.c0[a] = R(d.c0[a]);
+        c.dc[a] = R(d.dc[a]);
+        c.M0[a] = R(d.M0[a]);
+        c.M1[a] = R(d.M1[a]);
+    }
+    c.om_g = R(d.om_g);
+    c.om_f = R(d.om_f);
+    c.sw15 = R(d.sw15);
+    c.inv_W2 = R(d.inv_W2);
+    for (int i = 0; i < 3; ++i) c.g[i] = R(d.g[i]);
+}
+
 DevParams dev_params(const lbm_params* p, const Layout& L) {
     DevParams d{};
     d.nx = p->nx; d.ny = p->ny; d.nz = p->nz;
@@ -103,6 +120,8 @@ DevParams dev_params(const lbm_params* p, const Layout& L) {
     for (int i = 0; i < 3; ++i) d.g[i] = p->g[i];
     d.f_scale = p->f_scale > 0 ? p->f_scale : 1024.0;
     d.inv_f_scale = 1.0 / d.f_scale;
+    fill_coef(d, d.cd);
+    fill_coef(d, d.cf);
     return d;
 }
 
@@ -403,7 +422,8 @@ size_t lbm_adjoint_bytes(const lbm_params* p) {
 
 size_t lbm_adjoint_work_bytes(const lbm_params* p) {
     if (check_adjoint(p)) return 0;
-    return round_up((size_t)(lbm::adjoint_blocks() + 1) * lbm::adjoint_ntheta() * sizeof(double), kAlign);
+    const long long rows = lbm::adjoint_rows(dev_params(p, layout_of(p)));
+    return round_up((size_t)(rows + 1) * lbm::adjoint_ntheta() * sizeof(double), kAlign);
 }
 
 lbm_status lbm_adjoint_reset(const lbm_params* p, void* d_adj_work, void* stream) {
@@ -479,9 +499,10 @@ lbm_status lbm_adjoint_theta(const lbm_params* p, void* d_adj_work, double* out,
     if (!d_adj_work || !out) return fail(nullptr, LBM_ERR_ARG, "NULL buffer");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     double* partials = static_cast<double*>(d_adj_work);
-    double* dout = partials + (size_t)lbm::adjoint_blocks() * lbm::adjoint_ntheta();
+    const long long rows = lbm::adjoint_rows(dev_params(p, layout_of(p)));
+    double* dout = partials + (size_t)rows * lbm::adjoint_ntheta();
     cudaGetLastError();
-    lbm::launch_theta_final(partials, dout, s);
+    lbm::launch_theta_final(partials, int(rows), dout, s);
     lbm_status st = cuda_check(nullptr, "adjoint theta launch");
     if (st != LBM_OK) return st;
     cudaError_t e = cudaMemcpyAsync(out, dout, lbm::adjoint_ntheta() * sizeof(double), cudaMemcpyDeviceToHost, s);

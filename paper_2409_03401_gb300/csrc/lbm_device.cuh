@@ -12,6 +12,13 @@ namespace lbm {
 
 // ------------------------------------------------------------------------------------
 // Parameters as the kernels see them (derived once on the host from lbm_params).
+// Model coefficients in the working precision of a kernel (filled on the host from the
+// FP64 values below), so that FP32 kernels never convert an FP64 parameter per node.
+template <class R>
+struct Coef {
+    R lam, kphi, c0[2], dc[2], om_g, M0[2], M1[2], om_f, sw15, inv_W2, g[3];
+};
+
 struct DevParams {
     int nx, ny, nz;
     int wall_x, wall_z, source_off;
@@ -29,7 +36,13 @@ struct DevParams {
     double inv_W2;
     double g[3];          // buoyancy per unit phi
     double f_scale, inv_f_scale;
+    Coef<float> cf;
+    Coef<double> cd;
 };
+
+template <class R> __host__ __device__ __forceinline__ const Coef<R>& coef(const DevParams& P);
+template <> __host__ __device__ __forceinline__ const Coef<float>& coef<float>(const DevParams& P) { return P.cf; }
+template <> __host__ __device__ __forceinline__ const Coef<double>& coef<double>(const DevParams& P) { return P.cd; }
 
 // Pointers of one state buffer: population planes in the storage type, plus the FP32
 // rest-population planes used by 16-bit storage. ``plane`` lists every population plane
@@ -167,13 +180,13 @@ template <class R> __device__ __forceinline__ R dwell_d(R f) { return R(16) * f 
 // Eq. 33 written as mu = (c - c_0^eq) - p(phi) (c_1^eq - c_0^eq), since p(1 - phi) = 1 - p(phi).
 // The kernels carry the composition as its deviation dc = c - c_0^eq (see the h_0 storage).
 template <class R> __device__ __forceinline__ R closure_dev(R dc, R p, int a, const DevParams& P) {
-    return dc - p * R(P.dc[a]);
+    return dc - p * coef<R>(P).dc[a];
 }
 // Eq. 35 with Delta omega of Eq. 20 = sum mu (c_1^eq - c_0^eq)
 template <class R> __device__ __forceinline__ R source(R phi, R muA, R muB, const DevParams& P) {
     if (P.source_off) return R(0);
-    R dom = muA * R(P.dc[0]) + muB * R(P.dc[1]);
-    return R(P.kphi) * (-dwell_d(phi) + R(P.lam) * interp_dp(phi) * dom);
+    R dom = muA * coef<R>(P).dc[0] + muB * coef<R>(P).dc[1];
+    return coef<R>(P).kphi * (-dwell_d(phi) + coef<R>(P).lam * interp_dp(phi) * dom);
 }
 
 // ------------------------------------------------------------------------------------

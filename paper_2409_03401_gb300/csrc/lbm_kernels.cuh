@@ -14,6 +14,8 @@
 #include "lbm_device.cuh"
 #include "lbm_launch.h"
 
+#include <type_traits>
+
 namespace lbm {
 
 constexpr int kBlockX = 128;
@@ -87,6 +89,18 @@ struct Addr {
     }
 };
 
+// Pull addressing at a node whose whole neighbourhood (one node in x and y, and in z) lies
+// inside the lattice: no wrap and no wall, so the source of population k is node
+// self - e_k, an offset that is the same for every thread of a block.
+struct AddrInterior {
+    int self;
+    int sx, sxy;   // nx, nx * ny
+    __device__ __forceinline__ Slot src(int k, int ex, int ey, int ez) const {
+        return {self - ex - ey * sx - ez * sxy, k};
+    }
+    __device__ __forceinline__ Slot dst(int k, int, int, int) const { return {self, k}; }
+};
+
 // Incoming populations of one node and their moments (steps a1-a3 of one node).
 // The rest populations h_0 are stored shifted by c_0^eq (a constant shift commutes with
 // the BGK relaxation of Eq. 50), so sum_k h_k gives dc = c - c_0^eq without the
@@ -135,8 +149,8 @@ struct Node {
         S = source(phit, closure_dev(dcA, pt, 0, P), closure_dev(dcB, pt, 1, P), P);
     }
     __device__ __forceinline__ R phi() const { return phit + R(0.5) * S; }
-    __device__ __forceinline__ R cA(const DevParams& P) const { return dcA + R(P.c0[0]); }
-    __device__ __forceinline__ R cB(const DevParams& P) const { return dcB + R(P.c0[1]); }
+    __device__ __forceinline__ R cA(const DevParams& P) const { return dcA + coef<R>(P).c0[0]; }
+    __device__ __forceinline__ R cB(const DevParams& P) const { return dcB + coef<R>(P).c0[1]; }
 };
 
 // Eqs. 42-45 regrouped over opposite pairs: grad = 3 sum_k w_k e_k phi(x+e_k),
@@ -161,10 +175,10 @@ __device__ __forceinline__ void stencil(Get get, R phic, R& gx, R& gy, R& gz, R&
 template <class R>
 __device__ __forceinline__ void force_velocity(const R* f, R phi, R gx, R gy, R gz, R lap, const DevParams& P,
                                                R& Fx, R& Fy, R& Fz, R& ux, R& uy, R& uz) {
-    const R br = R(P.sw15) * (dwell_d(phi) * R(P.inv_W2) - lap);
-    Fx = br * gx + phi * R(P.g[0]);
-    Fy = br * gy + phi * R(P.g[1]);
-    Fz = br * gz + phi * R(P.g[2]);
+    const R br = coef<R>(P).sw15 * (dwell_d(phi) * coef<R>(P).inv_W2 - lap);
+    Fx = br * gx + phi * coef<R>(P).g[0];
+    Fy = br * gy + phi * coef<R>(P).g[1];
+    Fz = br * gz + phi * coef<R>(P).g[2];
     R jx = R(0), jy = R(0), jz = R(0);
 #pragma unroll
     for (int k = 1; k < 19; ++k) {
@@ -216,7 +230,7 @@ __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, type
         const R Ac = R(1) - R(1.5) * usq;
         const R Bc = ph - R(0.5) * usq;
         const R uF = ux * Fx + uy * Fy + uz * Fz;
-        const R omf = R(P.om_f);
+        const R omf = coef<R>(P).om_f;
         R f0post = R(0), resid = R(0);
 #pragma unroll
         for (int k = 0; k < 19; ++k) {
@@ -236,9 +250,9 @@ __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, type
     const R muA = closure_dev(nd.dcA, p, 0, P);
     const R muB = closure_dev(nd.dcB, p, 1, P);
     const R inv_cs2 = R(L::cs2() == 0.25 ? 4.0 : 3.0);
-    const R omg = R(P.om_g);
-    const R MA = R(P.M0[0]) * (R(1) - phi) + R(P.M1[0]) * phi;     // §2.3
-    const R MB = R(P.M0[1]) * (R(1) - phi) + R(P.M1[1]) * phi;
+    const R omg = coef<R>(P).om_g;
+    const R MA = coef<R>(P).M0[0] * (R(1) - phi) + coef<R>(P).M1[0] * phi;     // §2.3
+    const R MB = coef<R>(P).M0[1] * (R(1) - phi) + coef<R>(P).M1[1] * phi;
     const R omA = recip(MA * inv_cs2 + R(0.5));                      // tau_h = M / c_s^2
     const R omB = recip(MB * inv_cs2 + R(0.5));
     const R ga = phi - R(0.5) * nd.S;                                 // g^eq = w (ga + gb cu)
@@ -321,13 +335,15 @@ phi_kernel(const DevParams P, const StateView st, typename RealOf<T>::type* __re
 // chunk of z planes. At each plane z:
 //   fill(z + 1): every thread gathers the scalar populations (g, h^A, h^B) of its own
 //     column at plane z + 1, keeps them decoded in shared memory (double-buffered) with
-//     S and c - c_0^eq, and writes phi into a 3-plane ring; 84 threads add the ring's
+//     S and c - c_0^eq, and writes phi into a 4-plane ring; 84 threads add the ring's
 //     one-node halo.
 //   centre(z): gather the 19 f populations, take the scalar populations of plane z from
 //     shared memory, form the capillary stencil from the ring, collide and store f, then
 //     collide and store g, h^A, h^B (all stores local and coalesced).
-// The stencil therefore needs no separate pass and the scalar populations are read from
-// HBM once; the halo re-reads hit L2.
+// The ring holds four planes, so one barrier per plane suffices: fill(z + 2) overwrites the
+// plane of z - 2, which no thread can still be reading once all have passed the barrier
+// after fill(z + 1). The stencil therefore needs no separate pass and the scalar
+// populations are read from HBM once; the halo re-reads hit L2.
 constexpr int FX = 32, FY = 8, FT = FX * FY;
 constexpr int kHalo = 2 * (FX + 2) + 2 * FY;    // ring positions outside the tile (84)
 constexpr int kSPops = 3 * 7 + 3;               // 21 scalar populations + S, dcA, dcB
@@ -335,7 +351,7 @@ constexpr int kSPops = 3 * 7 + 3;               // 21 scalar populations + S, dc
 template <class T>
 __host__ __device__ constexpr size_t fused_smem_bytes() {
     using R = typename RealOf<T>::type;
-    return sizeof(R) * (3 * (FY + 2) * (FX + 2) + 2 * kSPops * FT);
+    return sizeof(R) * (4 * (FY + 2) * (FX + 2) + 2 * kSPops * FT);
 }
 
 template <class T>
@@ -346,7 +362,7 @@ fused_flow_kernel(const DevParams P, const StateView src, const StateView dst, i
     constexpr int Q = L::Q;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R (*ring)[FY + 2][FX + 2] = reinterpret_cast<R (*)[FY + 2][FX + 2]>(smem_raw);
-    R* spops = reinterpret_cast<R*>(smem_raw) + 3 * (FY + 2) * (FX + 2);   // [2][kSPops][FT]
+    R* spops = reinterpret_cast<R*>(smem_raw) + 4 * (FY + 2) * (FX + 2);   // [2][kSPops][FT]
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * FX + tx;
     const int x0 = blockIdx.x * FX, y0 = blockIdx.y * FY;
@@ -384,16 +400,27 @@ fused_flow_kernel(const DevParams P, const StateView src, const StateView dst, i
     Addr<PULL> own, halo;
     own.nb.init_xy(ox, oy, P);
     halo.nb.init_xy(hgx, hgy, P);
+    // blocks whose ring (tile + one-node halo) and its pull sources stay inside the lattice
+    // in x and y take the AddrInterior path on every plane z with 1 <= z <= nz - 2: one
+    // branch per plane, uniform across the block
+    const bool xy_inner = x0 >= 2 && x0 + FX + 2 <= P.nx && y0 >= 2 && y0 + FY + 2 <= P.ny;
+    const int sxy = P.nx * P.ny;
+    auto inner_plane = [&](int zr) { return xy_inner && zr >= 1 && zr <= P.nz - 2; };
 
     // phi (and, for a tile node, its scalar populations in buffer buf) of plane zz
-    auto fill = [&](int zz, int s, int buf) {
+    auto fill = [&](auto fast, int zz, int s, int buf) {
+        constexpr bool kFast = decltype(fast)::value;
         const int zr = zwrap(zz);
         R v = R(0);
         if (own_ok) {
-            own.self = node_of(ox, oy, zr, P);
-            own.nb.set_z(zr, P);
             Node<T, LAT_D3Q7, false> nd;
-            nd.gather_scalars(src, own, P);
+            if constexpr (kFast) {
+                nd.gather_scalars(src, AddrInterior{node_of(ox, oy, zr, P), P.nx, sxy}, P);
+            } else {
+                own.self = node_of(ox, oy, zr, P);
+                own.nb.set_z(zr, P);
+                nd.gather_scalars(src, own, P);
+            }
             nd.moments(P);
             v = nd.phi();
             if (active && buf >= 0) {
@@ -413,10 +440,14 @@ fused_flow_kernel(const DevParams P, const StateView src, const StateView dst, i
         if (tid < kHalo) {
             R hv = R(0);
             if (halo_ok) {
-                halo.self = node_of(hgx, hgy, zr, P);
-                halo.nb.set_z(zr, P);
                 Node<T, LAT_D3Q7, false> nd;
-                nd.gather_scalars(src, halo, P);
+                if constexpr (kFast) {
+                    nd.gather_scalars(src, AddrInterior{node_of(hgx, hgy, zr, P), P.nx, sxy}, P);
+                } else {
+                    halo.self = node_of(hgx, hgy, zr, P);
+                    halo.nb.set_z(zr, P);
+                    nd.gather_scalars(src, halo, P);
+                }
                 nd.moments(P);
                 hv = nd.phi();
             }
@@ -424,38 +455,51 @@ fused_flow_kernel(const DevParams P, const StateView src, const StateView dst, i
         }
     };
 
-    int sp = 0, sc = 1, sn = 2;   // ring slots of planes z - 1, z, z + 1
-    fill(zs - 1, sp, -1);
-    fill(zs, sc, zs & 1);
+    using Fast = std::true_type;
+    using Slow = std::false_type;
+    auto fill_any = [&](int zz, int s, int buf) {
+        if (inner_plane(zwrap(zz))) fill(Fast{}, zz, s, buf);
+        else fill(Slow{}, zz, s, buf);
+    };
+    // centre(z) of an active thread, with either addressing
+    auto centre = [&](const auto& ad, int z) {
+        const int sp = (z - 1) & 3, sc = z & 3, sn = (z + 1) & 3;
+        Node<T, LAT_D3Q7, true> nd;
+        nd.gather_flow(src, ad, P);
+        const R* spc = spops + (z & 1) * kSPops * FT + tid;
+        nd.S = spc[(3 * Q) * FT];
+        nd.dcA = spc[(3 * Q + 1) * FT];
+        nd.dcB = spc[(3 * Q + 2) * FT];
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            nd.g[k] = spc[k * FT];
+            nd.hA[k] = spc[(Q + k) * FT];
+            nd.hB[k] = spc[(2 * Q + k) * FT];
+        }
+        const R phi = ring[sc][ty + 1][tx + 1];
+        R gx, gy, gz, lap, Fx, Fy, Fz, ux, uy, uz;
+        stencil([&](int dx, int dy, int dz) {
+                    const int s = dz < 0 ? sp : (dz > 0 ? sn : sc);
+                    return ring[s][ty + 1 + dy][tx + 1 + dx];
+                }, phi, gx, gy, gz, lap);
+        force_velocity(nd.f, phi, gx, gy, gz, lap, P, Fx, Fy, Fz, ux, uy, uz);
+        collide_store(nd, phi, ux, uy, uz, Fx, Fy, Fz, dst, ad, P);
+    };
+
+    fill_any(zs - 1, (zs - 1) & 3, -1);
+    fill_any(zs, zs & 3, zs & 1);
     for (int z = zs; z < ze; ++z) {
-        fill(z + 1, sn, (z + 1) & 1);
+        fill_any(z + 1, (z + 1) & 3, (z + 1) & 1);
         __syncthreads();
         if (active) {
-            own.self = node_of(x, y, z, P);
-            own.nb.set_z(z, P);
-            Node<T, LAT_D3Q7, true> nd;
-            nd.gather_flow(src, own, P);
-            const R* spc = spops + (z & 1) * kSPops * FT + tid;
-            nd.S = spc[(3 * Q) * FT];
-            nd.dcA = spc[(3 * Q + 1) * FT];
-            nd.dcB = spc[(3 * Q + 2) * FT];
-#pragma unroll
-            for (int k = 0; k < Q; ++k) {
-                nd.g[k] = spc[k * FT];
-                nd.hA[k] = spc[(Q + k) * FT];
-                nd.hB[k] = spc[(2 * Q + k) * FT];
+            if (inner_plane(z)) {
+                centre(AddrInterior{node_of(x, y, z, P), P.nx, sxy}, z);
+            } else {
+                own.self = node_of(x, y, z, P);
+                own.nb.set_z(z, P);
+                centre(own, z);
             }
-            const R phi = ring[sc][ty + 1][tx + 1];
-            R gx, gy, gz, lap, Fx, Fy, Fz, ux, uy, uz;
-            stencil([&](int dx, int dy, int dz) {
-                        const int s = dz < 0 ? sp : (dz > 0 ? sn : sc);
-                        return ring[s][ty + 1 + dy][tx + 1 + dx];
-                    }, phi, gx, gy, gz, lap);
-            force_velocity(nd.f, phi, gx, gy, gz, lap, P, Fx, Fy, Fz, ux, uy, uz);
-            collide_store(nd, phi, ux, uy, uz, Fx, Fy, Fz, dst, own, P);
         }
-        __syncthreads();
-        const int t = sp; sp = sc; sc = sn; sn = t;
     }
 }
 

@@ -36,8 +36,8 @@ void launch_adjoint_seed(const DevParams&, const StateView&, int storage, int la
                          const void* muAb, const void* muBb, void* lam, double* partials, cudaStream_t);
 void launch_adjoint_init(const DevParams&, int storage, int lat, const double* phi0, const double* cA0,
                          const double* cB0, const void* lam, double* phi0b, double* partials, cudaStream_t);
-void launch_theta_final(const double* partials, double* out, cudaStream_t);
-int adjoint_blocks();
+void launch_theta_final(const double* partials, int rows, double* out, cudaStream_t);
+long long adjoint_rows(const DevParams& P);
 int adjoint_ntheta();
 
 LBM_DECLARE_LAUNCHERS(f64)

@@ -68,6 +68,17 @@ def test_flow_fp64_tight(inplace):
     _close(compare(p.with_(inplace=inplace), fields(), 30), TOL["f64"])
 
 
+@pytest.mark.parametrize("storage,wall_x", [("f64", False), ("f32", False), ("f32", True)])
+def test_flow_interior_and_edge_blocks(storage, wall_x):
+    # 100 x 30 x 12: the fused kernel's blocks at x0 = 32, 64 and y0 = 8, 16 have their whole
+    # halo inside the lattice and take the interior addressing on planes 1..10, the others
+    # and planes 0 and 11 (periodic wrap in z) take the general one; FP64 pins both to
+    # round-off
+    p, fields = configs.ripening(shape=(12, 30, 100), storage=storage)
+    q = p.with_(flow=True, wall_x=wall_x)
+    _close(compare(q, fields(), 12), TOL[storage])
+
+
 def test_flow_periodic_z_fp32():
     # flow without walls: periodic wrap of the fused kernel's z ring
     p, fields = configs.ripening(shape=(20, 18, 36))
