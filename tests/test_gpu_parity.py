@@ -44,7 +44,7 @@ def test_ripening_fp32_long():
 @pytest.mark.parametrize("steps", [1, 2, 25])
 def test_sedimentation_flow_fp32(steps, inplace):
     # 140 x 20 x 18: several 32 x 8 tiles and 128-thread rows with ragged tails in x and y,
-    # and a z extent that is not a multiple of the 64-plane chunk
+    # and a z extent that is not a multiple of the 32-plane chunk
     p, fields = configs.sedimentation(shape=(18, 20, 140), fraction=0.05, r=(3.0, 5.0))
     _close(compare(p.with_(inplace=inplace), fields(), steps), TOL["f32"])
 
@@ -56,7 +56,7 @@ def test_sedimentation_flow_fp32_long(inplace):
 
 
 def test_flow_fp32_z_chunks():
-    # 150 planes: three 64-plane chunks of the fused kernel, the last one ragged
+    # 150 planes: five 32-plane chunks of the fused kernel, the last one ragged (22)
     p, fields = configs.sedimentation(shape=(150, 12, 20), fraction=0.04, r=(3.0, 4.0))
     _close(compare(p, fields(), 6), TOL["f32"])
 
