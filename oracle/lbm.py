@@ -231,6 +231,22 @@ class OracleLBM:
                                                      - usq / (2.0 * lat.cs2))) - 0.5 * Fk[k])
         return torch.stack(parts)
 
+    def _trt(self, f, f_eq, Fk, om_plus):
+        """Two-relaxation-time collision of the flow populations (the TRT operator that the
+        paper names as an alternative to BGK, §3): the parts of f - f^eq that are even and
+        odd under k -> opp(k) relax at omega+ and omega-. omega+ is the BGK rate of Eq. 36
+        (it sets nu); omega- follows from the magic parameter
+        Lambda = (1/omega+ - 1/2)(1/omega- - 1/2). f^eq is Eq. 39 with its -F_k/2, and F_k is
+        added as in Eq. 36, so omega- = omega+ gives back the BGK update exactly."""
+        lam = self.p.trt_magic
+        om_minus = 1.0 / (lam / (1.0 / om_plus - 0.5) + 0.5)
+        opp = [D3Q19.opposite(k) for k in range(D3Q19.Q)]
+        d = f - f_eq
+        d_bar = d[opp]
+        even = 0.5 * (d + d_bar)
+        odd = 0.5 * (d - d_bar)
+        return f - om_plus * even - om_minus * odd + Fk
+
     # ---------------------------------------------------------------- step
     def step(self, n=1):
         for _ in range(n):
@@ -263,7 +279,10 @@ class OracleLBM:
             Fk = self._forcing(u, mac["F"])
             f_eq = self._f_eq(mac["p"], u, Fk)
             om_f = m.relaxation_rate(p.nu, D3Q19.cs2)
-            f_post = self.f - om_f * (self.f - f_eq) + Fk
+            if p.collision == "TRT":
+                f_post = self._trt(self.f, f_eq, Fk, om_f)
+            else:
+                f_post = self.f - om_f * (self.f - f_eq) + Fk
             self.f = self._stream(f_post, D3Q19)
         self.g = self._stream(g_post, ls)
         self.hA = self._stream(h_post[0], ls)

@@ -9,12 +9,14 @@ equilibrium compositions of phase pi in {0, 1} for component alpha in {A, B},
 M[pi][alpha] the scaled species mobility of component alpha in phase pi (the
 diffusivity of the bulk phase, §2.3), nu the kinematic viscosity, sigma the
 surface tension, g the buoyancy acceleration times the density contrast
-(F_g = phi * g, §2.5).
+(F_g = phi * g, §2.5). collision selects the flow collision operator: the paper's BGK,
+or the two-relaxation-time operator it names as an alternative (§3).
 """
 from dataclasses import dataclass, field, asdict, replace
 from typing import Tuple
 
 LATTICES = ("D2Q5", "D3Q7")
+COLLISIONS = ("BGK", "TRT")
 STORAGES = ("f64", "f32", "f16", "bf16")
 
 
@@ -39,6 +41,8 @@ class LBMParams:
     sigma: float = 1.0e-3
     g: Tuple[float, float, float] = (0.0, 0.0, -1.0e-5)
     f_scale: float = 1024.0        # 16-bit storage: scale applied to f_k / w_k before rounding
+    collision: str = "BGK"         # flow collision: "BGK" (one rate) or "TRT" (two rates)
+    trt_magic: float = 3.0 / 16.0  # TRT: Lambda = (1/omega+ - 1/2)(1/omega- - 1/2)
 
     def __post_init__(self):
         if self.lattice not in LATTICES:
@@ -49,6 +53,10 @@ class LBMParams:
             raise ValueError("lattice extents must be >= 1")
         if self.lattice == "D2Q5" and self.nz != 1:
             raise ValueError("D2Q5 needs nz == 1")
+        if self.collision not in COLLISIONS:
+            raise ValueError(f"collision must be one of {COLLISIONS}")
+        if not self.trt_magic > 0:
+            raise ValueError("trt_magic must be > 0")
         if self.flow and self.lattice != "D3Q7":
             raise ValueError("flow is implemented on 3D lattices (D3Q19 + D3Q7)")
 
