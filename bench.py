@@ -31,7 +31,7 @@ ALG_BYTES_PER_NODE = {"f32": 320.0, "f16": 176.0, "bf16": 176.0, "f64": 640.0}
 # DRAM bytes (read + write) per node of one fused_flow_kernel<float> launch, from an ncu capture
 # of this kernel at 192^3 (profiles/fused_flow_kernel_f32_192cube.md); traffic scales with the
 # node count. Set to None whenever the kernel changes until it is captured again.
-NCU_DRAM_BYTES_PER_NODE_F32 = 164.23 + 153.88
+NCU_DRAM_BYTES_PER_NODE_F32 = None
 
 
 def parse():
@@ -303,6 +303,16 @@ def gb300(args):
                             "roofline_frac": vb / (vstep / 1e3) / 1e9 / peak}
             del v
             torch.cuda.synchronize()
+        # the two-relaxation-time flow collision on the same workload, FP32 storage
+        q = p.with_(collision="TRT")
+        v = Simulation(q, *init, device=device)
+        vs = max(20, args.steps // 2)
+        vms, _, vstep = time_device(v, vs, args.warmup, dist)
+        var["trt"] = {"value": ws * nodes * vs / (vms / 1e3) / 1e6, "unit": "MLUPS", "ms_per_step": vms / vs,
+                      "speedup_vs_f32": (ms / args.steps) / (vms / vs), "collision": "TRT, Lambda = 3/16",
+                      "roofline_frac": ALG_BYTES_PER_NODE["f32"] * nodes / (vstep / 1e3) / 1e9 / peak}
+        del v
+        torch.cuda.synchronize()
         out["variants"] = var
 
     if not args.no_variants:

@@ -52,6 +52,12 @@ typedef enum { LBM_D2Q5 = 0, LBM_D3Q7 = 1 } lbm_lattice;
 typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16 = 2, LBM_BF16 = 3 } lbm_storage;
 
 /* Model parameters in lattice units (dx = dt = 1, rho_0 = 1), named as in the paper. */
+/* Flow collision operators. LBM_BGK is the paper's single-rate operator (Eq. 36). LBM_TRT is
+ * the two-relaxation-time operator the paper names as an alternative (§3): the parts of
+ * f - f^eq even and odd under k -> opp(k) relax at omega+ and omega-; f^eq keeps the
+ * -F_k/2 shift of Eq. 39 and F_k is added as in Eq. 36. */
+typedef enum { LBM_BGK = 0, LBM_TRT = 1 } lbm_collision;
+
 typedef struct lbm_params {
     int32_t nx, ny, nz;      /* lattice extents; nz = 1 with LBM_D2Q5 */
     int32_t lattice;         /* lbm_lattice of g, h^A, h^B */
@@ -73,6 +79,9 @@ typedef struct lbm_params {
     double sigma;            /* surface tension in Eq. 34 */
     double g[3];             /* buoyancy per unit phi: F_g = phi * g (§2.5, Delta rho g / rho_0) */
     double f_scale;          /* 16-bit storage scale of f_k / w_k: 0 or 1024 (fixed at 1024) */
+    int32_t collision;       /* flow collision, lbm_collision: LBM_BGK (Eq. 36) or LBM_TRT */
+    double trt_magic;        /* LBM_TRT: Lambda = (1/omega+ - 1/2)(1/omega- - 1/2) > 0, where omega+
+                              * is the BGK rate of Eq. 36 (it sets nu); 0 selects 3/16 */
 } lbm_params;
 
 /* Indices of lbm_fields outputs. */

@@ -14,6 +14,8 @@ LBM_D2Q5, LBM_D3Q7 = 0, 1
 LBM_F64, LBM_F32, LBM_F16, LBM_BF16 = 0, 1, 2, 3
 STORAGE = {"f64": LBM_F64, "f32": LBM_F32, "f16": LBM_F16, "bf16": LBM_BF16}
 LATTICE = {"D2Q5": LBM_D2Q5, "D3Q7": LBM_D3Q7}
+LBM_BGK, LBM_TRT = 0, 1
+COLLISION = {"BGK": LBM_BGK, "TRT": LBM_TRT}
 FIELDS = ("phi", "muA", "muB", "cA", "cB", "p", "ux", "uy", "uz", "S")
 REDUCTIONS = ("phi", "cA", "cB", "p", "S", "umax", "g", "nonfinite")
 NFIELDS = len(FIELDS)
@@ -30,6 +32,7 @@ class lbm_params(ctypes.Structure):
         ("c_eq", (ctypes.c_double * 2) * 2), ("M", (ctypes.c_double * 2) * 2),
         ("nu", ctypes.c_double), ("sigma", ctypes.c_double), ("g", ctypes.c_double * 3),
         ("f_scale", ctypes.c_double),
+        ("collision", ctypes.c_int32), ("trt_magic", ctypes.c_double),
     ]
 
 
@@ -124,4 +127,6 @@ def make_params(p):
     for i in range(3):
         c.g[i] = p.g[i]
     c.f_scale = p.f_scale
+    c.collision = COLLISION[p.collision]
+    c.trt_magic = p.trt_magic
     return c

@@ -16,12 +16,13 @@ namespace lbm {
 // FP64 values below), so that FP32 kernels never convert an FP64 parameter per node.
 template <class R>
 struct Coef {
-    R lam, kphi, c0[2], dc[2], om_g, M0[2], M1[2], om_f, sw15, inv_W2, g[3];
+    R lam, kphi, c0[2], dc[2], om_g, M0[2], M1[2], om_f, om_fm, sw15, inv_W2, g[3];
 };
 
 struct DevParams {
     int nx, ny, nz;
     int wall_x, wall_z, source_off;
+    int trt;              // flow collision: 0 BGK (Eq. 36), 1 two-relaxation-time
     long long n;          // nodes
     long long plane;      // elements between two population planes (n rounded up)
     double W, lam;
@@ -32,6 +33,7 @@ struct DevParams {
     double M0[2], M1[2];  // mobilities of phase 0 and 1 per component (§2.3)
     double inv_cs2;       // 1 / c_s^2 of the scalar lattice
     double om_f;          // 1 / (nu / c_s^2 + 1/2)  (Eq. 36), c_s^2 = 1/3
+    double om_fm;         // TRT rate of the odd part: 1 / (Lambda / (1/om_f - 1/2) + 1/2)
     double sw15;          // (3/2) sigma W  (Eq. 34)
     double inv_W2;
     double g[3];          // buoyancy per unit phi

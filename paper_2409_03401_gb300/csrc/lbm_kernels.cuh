@@ -232,17 +232,41 @@ __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, type
         const R uF = ux * Fx + uy * Fy + uz * Fz;
         const R omf = coef<R>(P).om_f;
         R f0post = R(0), resid = R(0);
-#pragma unroll
-        for (int k = 0; k < 19; ++k) {
+        // forcing term F_k (Eqs. 37-38) and shifted equilibrium (Eq. 39) of direction k
+        auto force_eq = [&](int k, R& Fk, R& feq) {
             const int ex = D3Q19::ex(k), ey = D3Q19::ey(k), ez = D3Q19::ez(k);
             const R w = R(D3Q19::w(k));
             const R cu = edot(ex, ey, ez, ux, uy, uz);
-            const R Fk = w * (Ac + cu * (R(3) + R(4.5) * cu)) * (edot(ex, ey, ez, Fx, Fy, Fz) - uF);
-            const R feq = w * (Bc + cu * (R(1) + R(1.5) * cu)) - R(0.5) * Fk;
-            const R post = nd.f[k] - omf * (nd.f[k] - feq) + Fk;
-            if (is16<T>() && k == 0) { f0post = post; continue; }
-            const Slot s = ad.dst(k, ex, ey, ez);
+            Fk = w * (Ac + cu * (R(3) + R(4.5) * cu)) * (edot(ex, ey, ez, Fx, Fy, Fz) - uF);
+            feq = w * (Bc + cu * (R(1) + R(1.5) * cu)) - R(0.5) * Fk;
+        };
+        auto put = [&](int k, R post) {
+            if (is16<T>() && k == 0) { f0post = post; return; }
+            const Slot s = ad.dst(k, D3Q19::ex(k), D3Q19::ey(k), D3Q19::ez(k));
             resid += Codec<T>::template store_residual<SET_F>(element<T, 0>(out, k, s), post, D3Q19::w(k), P);
+        };
+        if (!P.trt) {                                     // BGK, Eq. 36
+#pragma unroll
+            for (int k = 0; k < 19; ++k) {
+                R Fk, feq;
+                force_eq(k, Fk, feq);
+                put(k, nd.f[k] - omf * (nd.f[k] - feq) + Fk);
+            }
+        } else {                                          // two relaxation times
+            const R omm = coef<R>(P).om_fm;
+            R F0, feq0;
+            force_eq(0, F0, feq0);
+            put(0, nd.f[0] - omf * (nd.f[0] - feq0) + F0);
+#pragma unroll
+            for (int k = 1; k < 19; k += 2) {             // pairs (k, opp(k) = k + 1)
+                R Fa, ea, Fb, eb;
+                force_eq(k, Fa, ea);
+                force_eq(k + 1, Fb, eb);
+                const R da = nd.f[k] - ea, db = nd.f[k + 1] - eb;
+                const R even = R(0.5) * (da + db), odd = R(0.5) * (da - db);
+                put(k, nd.f[k] - omf * even - omm * odd + Fa);
+                put(k + 1, nd.f[k + 1] - omf * even + omm * odd + Fb);
+            }
         }
         if (is16<T>()) out.rest[3 * P.plane + self] = float(f0post + resid);
     }

@@ -64,3 +64,15 @@ def test_sizes_and_validation_on_the_host(lib):
     assert st == _lib.LBM_ERR_ARG and b"aligned" in lib.lbm_last_error(None)
     assert lib.lbm_step(None, 1) == _lib.LBM_ERR_ARG
     assert lib.lbm_time(None) == -1
+    # collision operator: TRT keeps the state size; an unknown operator or a negative
+    # magic parameter is rejected before any device work
+    trt = _lib.make_params(p.with_(collision="TRT"))
+    assert lib.lbm_state_bytes(ctypes.byref(trt)) == state
+    for field, value in (("collision", 2), ("trt_magic", -1.0)):
+        badc = _lib.make_params(p.with_(collision="TRT"))
+        setattr(badc, field, value)
+        assert lib.lbm_state_bytes(ctypes.byref(badc)) == 0
+        st = lib.lbm_init(ctypes.byref(badc), ctypes.c_void_p(256), ctypes.c_void_p(256), ctypes.c_void_p(8),
+                          ctypes.c_void_p(8), ctypes.c_void_p(8), None, ctypes.byref(ctx))
+        assert st == _lib.LBM_ERR_ARG
+        assert field.encode() in lib.lbm_last_error(None)

@@ -79,6 +79,16 @@ def test_flow_interior_and_edge_blocks(storage, wall_x):
     _close(compare(q, fields(), 12), TOL[storage])
 
 
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("inplace", [False, True])
+def test_flow_trt(storage, inplace):
+    # two-relaxation-time flow collision (Lambda = 3/16, and nu = 0.05 so that omega- differs
+    # strongly from omega+) on both flow layouts, walls at the z ends and interior blocks
+    p, fields = configs.sedimentation(shape=(14, 20, 100), fraction=0.05, r=(3.0, 5.0), storage=storage)
+    q = p.with_(collision="TRT", nu=0.05, inplace=inplace)
+    _close(compare(q, fields(), 15), TOL[storage])
+
+
 def test_flow_periodic_z_fp32():
     # flow without walls: periodic wrap of the fused kernel's z ring
     p, fields = configs.ripening(shape=(20, 18, 36))
