@@ -22,9 +22,10 @@ buffer; the two schemes share nothing but the equations):
 Readings of points the paper leaves open (each stated where it is used):
   * the implicit phi moment of Eq. 49 is evaluated in one explicit pass, the
     source taken at phi~ = sum g;
-  * phi, c^A, c^B use D2Q5 (2D) or D3Q7 (3D) with their own c_s^2 (1/3 and
-    1/4) wherever the equations write c_s^2 for those populations; the flow
-    and the phi stencil use D3Q19 (c_s^2 = 1/3, the "3" of Eqs. 43 and 45);
+  * phi, c^A, c^B use D2Q5 (2D), D3Q7 or D3Q19 (3D; D3Q19 is the paper's own
+    choice for every equation) with their own c_s^2 (1/3, 1/4, 1/3) wherever
+    the equations write c_s^2 for those populations; the flow and the phi
+    stencil use D3Q19 (c_s^2 = 1/3, the "3" of Eqs. 43 and 45);
   * the stencil sees phi of step 3 at every neighbour; across a wall it sees
     the mirror value (zero normal gradient, §4.2.4);
   * tau is the paper's, D = tau c_s^2, so the BGK rate is 1/(tau + 1/2);

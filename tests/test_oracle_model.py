@@ -162,11 +162,12 @@ def _random_node_state(seed, flow=True):
     return phi, c, mu, u, F, S, ph
 
 
-def test_equilibrium_moment_identities():
-    p = LBMParams(nx=3, ny=2, nz=1, lattice="D3Q7", flow=True)
+@pytest.mark.parametrize("lattice", ["D3Q7", "D3Q19"])
+def test_equilibrium_moment_identities(lattice):
+    p = LBMParams(nx=3, ny=2, nz=1, lattice=lattice, flow=True)
     o = OracleLBM(p)
     phi, c, mu, u, F, S, ph = _random_node_state(1)
-    ls = L.D3Q7
+    ls = L.BY_NAME[lattice]
     es = ls.e_tensor()
     # Eq. 51: sum h = c, sum h e = c u, sum h e e = c_s^2 mu I
     h = o._h_eq(c, mu, u)

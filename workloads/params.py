@@ -15,7 +15,7 @@ or the two-relaxation-time operator it names as an alternative (§3).
 from dataclasses import dataclass, field, asdict, replace
 from typing import Tuple
 
-LATTICES = ("D2Q5", "D3Q7")
+LATTICES = ("D2Q5", "D3Q7", "D3Q19")
 COLLISIONS = ("BGK", "TRT")
 STORAGES = ("f64", "f32", "f16", "bf16")
 
@@ -25,7 +25,7 @@ class LBMParams:
     nx: int
     ny: int
     nz: int
-    lattice: str = "D3Q7"          # lattice of the phi, c^A, c^B equations
+    lattice: str = "D3Q7"          # lattice of the phi, c^A, c^B equations (D3Q19: the paper's choice)
     flow: bool = False             # D3Q19 flow populations with capillary + buoyancy forcing
     storage: str = "f32"           # population storage type on the GPU (oracle is always FP64)
     wall_x: bool = False           # half-way bounce-back planes at x = -1/2 and x = nx - 1/2
@@ -57,8 +57,8 @@ class LBMParams:
             raise ValueError(f"collision must be one of {COLLISIONS}")
         if not self.trt_magic > 0:
             raise ValueError("trt_magic must be > 0")
-        if self.flow and self.lattice != "D3Q7":
-            raise ValueError("flow is implemented on 3D lattices (D3Q19 + D3Q7)")
+        if self.flow and self.lattice == "D2Q5":
+            raise ValueError("flow is implemented on 3D lattices (D3Q19 flow + D3Q7 or D3Q19 scalars)")
 
     @property
     def shape(self):
