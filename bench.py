@@ -313,6 +313,18 @@ def gb300(args):
                       "roofline_frac": ALG_BYTES_PER_NODE["f32"] * nodes / (vstep / 1e3) / 1e9 / peak}
         del v
         torch.cuda.synchronize()
+        # D3Q19 for phi, c^A, c^B (the paper's lattice for every equation): 76 populations,
+        # phi pass + per-node pull step, FP32 storage
+        q = p.with_(lattice="D3Q19")
+        v = Simulation(q, *init, device=device)
+        vs = max(10, args.steps // 10)
+        vms, _, _ = time_device(v, vs, args.warmup, dist)
+        b19 = 2 * 76 * 4.0
+        var["d3q19_scalars"] = {"value": ws * nodes * vs / (vms / 1e3) / 1e6, "unit": "MLUPS", "ms_per_step": vms / vs,
+                                "alg_bytes_per_node": b19, "kernels": "phi_kernel + step_kernel (pull)",
+                                "roofline_frac": b19 * nodes / (vms / vs / 1e3) / 1e9 / peak}
+        del v
+        torch.cuda.synchronize()
         out["variants"] = var
 
     if not args.no_variants:

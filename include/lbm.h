@@ -38,7 +38,11 @@ typedef enum {
     LBM_ERR_STATE = -4      /* call out of order (e.g. adjoint on a flow lattice) */
 } lbm_status;
 
-typedef enum { LBM_D2Q5 = 0, LBM_D3Q7 = 1 } lbm_lattice;
+/* Lattice of the phi, c^A and c^B populations (the flow always uses D3Q19). LBM_D2Q5 and
+ * LBM_D3Q7 are the minimal advection-diffusion sets; LBM_D3Q19 is the paper's choice for
+ * every equation (§3). With flow and two state copies, LBM_D3Q7 runs the fused z-marching
+ * kernel; LBM_D3Q19 runs a phi pass and a per-node pull step instead. */
+typedef enum { LBM_D2Q5 = 0, LBM_D3Q7 = 1, LBM_D3Q19 = 2 } lbm_lattice;
 
 /* Storage type of the populations. Arithmetic is FP64 for LBM_F64 and FP32 otherwise.
  * LBM_F16 / LBM_BF16 store every moving population as a 16-bit deviation from its

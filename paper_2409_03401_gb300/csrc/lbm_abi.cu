@@ -19,7 +19,9 @@ constexpr int kRedBlocks = 1216;   // 152 SMs x 8 blocks of 256 threads
 
 long long round_up(long long v, long long a) { return (v + a - 1) / a * a; }
 
-int scalar_q(int lattice) { return lattice == LBM_D2Q5 ? 5 : 7; }
+int scalar_q(int lattice) { return lattice == LBM_D2Q5 ? 5 : (lattice == LBM_D3Q19 ? 19 : 7); }
+// the fused z-marching flow kernel is written for D3Q7 scalar sets
+bool fused_flow(const lbm_params* p) { return p->lattice == LBM_D3Q7; }
 size_t storage_size(int s) { return s == LBM_F64 ? 8 : (s == LBM_F32 ? 4 : 2); }
 bool is16(int s) { return s == LBM_F16 || s == LBM_BF16; }
 
@@ -39,10 +41,11 @@ const char* check_params(const lbm_params* p) {
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) return "lattice extents must be >= 1";
     if (p->ny > 65535 || p->nz > 65535) return "ny and nz must be <= 65535";
     if ((long long)p->nx * p->ny * p->nz >= (1LL << 31)) return "nx*ny*nz must be < 2^31";
-    if (p->lattice != LBM_D2Q5 && p->lattice != LBM_D3Q7) return "lattice must be LBM_D2Q5 or LBM_D3Q7";
+    if (p->lattice != LBM_D2Q5 && p->lattice != LBM_D3Q7 && p->lattice != LBM_D3Q19)
+        return "lattice must be LBM_D2Q5, LBM_D3Q7 or LBM_D3Q19";
     if (p->lattice == LBM_D2Q5 && p->nz != 1) return "LBM_D2Q5 needs nz == 1";
     if (p->flow != 0 && p->flow != 1) return "flow must be 0 or 1";
-    if (p->flow && p->lattice != LBM_D3Q7) return "flow needs the 3D lattice (LBM_D3Q7 scalars, D3Q19 flow)";
+    if (p->flow && p->lattice == LBM_D2Q5) return "flow needs a 3D scalar lattice (LBM_D3Q7 or LBM_D3Q19)";
     if (p->storage < LBM_F64 || p->storage > LBM_BF16) return "storage must be one of lbm_storage";
     if (p->inplace != 0 && p->inplace != 1) return "inplace must be 0 or 1";
     if (!(p->W > 0)) return "W must be > 0";
@@ -107,7 +110,7 @@ DevParams dev_params(const lbm_params* p, const Layout& L) {
     d.n = L.n; d.plane = L.plane;
     d.W = p->W; d.lam = p->lambda;
     d.kphi = p->M_phi / (p->W * p->W);
-    const double cs2 = p->lattice == LBM_D2Q5 ? 1.0 / 3.0 : 0.25;
+    const double cs2 = p->lattice == LBM_D3Q7 ? 0.25 : 1.0 / 3.0;
     d.inv_cs2 = 1.0 / cs2;
     for (int a = 0; a < 2; ++a) {
         d.c0[a] = p->c_eq[0][a];
@@ -202,9 +205,9 @@ StateView view_of(const lbm_params* p, const Layout& L, void* base) {
     v.rest = is16(p->storage) ? reinterpret_cast<float*>(s + L.off_rest) : nullptr;
     for (int k = 0; k < 19; ++k) v.plane[k] = p->flow ? s + L.off_f + k * pb : nullptr;
     for (int k = 0; k < Q; ++k) {
-        v.plane[lbm::kPlaneG + k] = s + L.off_g + k * pb;
-        v.plane[lbm::kPlaneHA + k] = s + L.off_hA + k * pb;
-        v.plane[lbm::kPlaneHB + k] = s + L.off_hB + k * pb;
+        v.plane[19 + k] = s + L.off_g + k * pb;              // Planes<LAT>::G, HA, HB
+        v.plane[19 + Q + k] = s + L.off_hA + k * pb;
+        v.plane[19 + 2 * Q + k] = s + L.off_hB + k * pb;
     }
     return v;
 }
@@ -295,17 +298,19 @@ lbm_status lbm_step(lbm_ctx* c, int nsteps) {
         const bool timed = c->prof_n < c->prof_max;
         cudaEvent_t* e = timed ? &c->ev[3 * c->prof_n] : nullptr;
         if (timed) cudaEventRecord(e[0], c->stream);
-        if (c->p.flow && !c->L.two) {
-            LBM_DISPATCH(c->p.storage, launch_phi, c->dp, c->st, c->p.lattice, mode, c->work + c->L.off_phi,
+        // src holds time level t; dst receives t + 1 (the same buffer in the in-place layout)
+        const StateView& src = current(c);
+        const StateView& dst = c->L.two ? ((c->t & 1) ? c->st : c->st1) : c->st;
+        const bool fused = c->L.two && fused_flow(&c->p);
+        if (c->p.flow && !fused) {
+            LBM_DISPATCH(c->p.storage, launch_phi, c->dp, src, c->p.lattice, mode, c->work + c->L.off_phi,
                          c->stream);
         }
         if (timed) cudaEventRecord(e[1], c->stream);
-        if (c->L.two) {
-            const StateView& src = current(c);
-            const StateView& dst = (c->t & 1) ? c->st : c->st1;
+        if (fused) {
             LBM_DISPATCH(c->p.storage, launch_fused, c->dp, src, dst, zchunk_of(&c->p), c->stream);
         } else {
-            LBM_DISPATCH(c->p.storage, launch_step, c->dp, c->st, c->st, c->p.lattice, c->p.flow != 0, mode,
+            LBM_DISPATCH(c->p.storage, launch_step, c->dp, src, dst, c->p.lattice, c->p.flow != 0, mode,
                          c->work + c->L.off_phi, c->stream);
         }
         if (timed) { cudaEventRecord(e[2], c->stream); c->prof_n += 1; }
@@ -350,7 +355,9 @@ lbm_status lbm_profile_end(lbm_ctx* c, double* out) {
     return cuda_check(c, "profile events");
 }
 
-int lbm_kernels_per_step(const lbm_ctx* c) { return c ? ((c->p.flow && !c->L.two) ? 2 : 1) : 0; }
+int lbm_kernels_per_step(const lbm_ctx* c) {
+    return c ? ((c->p.flow && !(c->L.two && fused_flow(&c->p))) ? 2 : 1) : 0;
+}
 
 int64_t lbm_time(const lbm_ctx* c) { return c ? c->t : -1; }
 
@@ -395,16 +402,16 @@ lbm_status lbm_step_buffers(const lbm_params* p, const void* d_src, void* d_dst,
     if (!d_src || !d_dst || t < 0) return fail(nullptr, LBM_ERR_ARG, "buffers must be non-NULL and t >= 0");
     if (d_src == d_dst) return fail(nullptr, LBM_ERR_ARG, "d_src and d_dst must differ");
     const Layout L = layout_of(p);
-    if (p->flow && p->inplace && !d_work) return fail(nullptr, LBM_ERR_ARG, "in-place flow needs d_work");
+    if (p->flow && !(L.two && fused_flow(p)) && !d_work) return fail(nullptr, LBM_ERR_ARG, "this flow step needs d_work (phi pass)");
     const DevParams dp = dev_params(p, L);
     const StateView src = view_of(p, L, const_cast<void*>(d_src));
     const StateView dst = view_of(p, L, d_dst);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaGetLastError();
-    if (L.two) {
+    if (L.two && fused_flow(p)) {
         LBM_DISPATCH(p->storage, launch_fused, dp, src, dst, zchunk_of(p), s);
     } else {
-        const int mode = (t & 1) ? lbm::kModeAAOdd : lbm::kModeAAEven;
+        const int mode = L.two ? lbm::kModePull : ((t & 1) ? lbm::kModeAAOdd : lbm::kModeAAEven);
         char* phi = static_cast<char*>(d_work) + L.off_phi;
         if (p->flow) { LBM_DISPATCH(p->storage, launch_phi, dp, src, p->lattice, mode, phi, s); }
         LBM_DISPATCH(p->storage, launch_step, dp, src, dst, p->lattice, p->flow != 0, mode, phi, s);

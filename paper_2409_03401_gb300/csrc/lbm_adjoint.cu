@@ -67,7 +67,7 @@ __device__ __forceinline__ void collide_adjoint(const Node<T, LAT, false>& nd,
     using R = typename RealOf<T>::type;
     using L = Scalar<LAT>;
     constexpr int Q = L::Q;
-    const R inv_cs2 = R(L::cs2() == 0.25 ? 4.0 : 3.0);
+    const R inv_cs2 = R(1.0 / L::cs2());
     // forward quantities (as in collide_store with u = 0)
     const R S = nd.S;
     const R phi = nd.phi();
@@ -351,9 +351,13 @@ void adjoint_init_T(const DevParams& P, const double* phi0, const double* cA0, c
 #define LBM_ADJ_DISPATCH(STORAGE, LAT, FN, ...)                                                 \
     do {                                                                                        \
         if (STORAGE == 0) {                                                                     \
-            if (LAT == LAT_D2Q5) FN<double, LAT_D2Q5>(__VA_ARGS__); else FN<double, LAT_D3Q7>(__VA_ARGS__); \
+            if (LAT == LAT_D2Q5) FN<double, LAT_D2Q5>(__VA_ARGS__);                             \
+            else if (LAT == LAT_D3Q19) FN<double, LAT_D3Q19>(__VA_ARGS__);                      \
+            else FN<double, LAT_D3Q7>(__VA_ARGS__);                                             \
         } else {                                                                                \
-            if (LAT == LAT_D2Q5) FN<float, LAT_D2Q5>(__VA_ARGS__); else FN<float, LAT_D3Q7>(__VA_ARGS__);   \
+            if (LAT == LAT_D2Q5) FN<float, LAT_D2Q5>(__VA_ARGS__);                              \
+            else if (LAT == LAT_D3Q19) FN<float, LAT_D3Q19>(__VA_ARGS__);                       \
+            else FN<float, LAT_D3Q7>(__VA_ARGS__);                                              \
         }                                                                                       \
     } while (0)
 

@@ -48,10 +48,10 @@ template <> __host__ __device__ __forceinline__ const Coef<double>& coef<double>
 
 // Pointers of one state buffer: population planes in the storage type, plus the FP32
 // rest-population planes used by 16-bit storage. ``plane`` lists every population plane
-// (f_0..f_18, then g, h^A, h^B from kPlaneG, kPlaneHA, kPlaneHB) so that a kernel can
+// (f_0..f_18, then the Q planes of g, h^A and h^B: Planes<LAT>) so that a kernel can
 // address population k of node n as plane[k] + n, the pointer coming straight from the
 // kernel's parameter space.
-constexpr int kPlaneG = 19, kPlaneHA = 26, kPlaneHB = 33, kPlanes = 40;
+constexpr int kPlanes = 19 + 3 * 19;   // room for D3Q19 scalar sets
 struct StateView {
     void* f;      // 19 planes (flow only)
     void* g;      // Q planes
@@ -61,7 +61,7 @@ struct StateView {
     void* plane[kPlanes];
 };
 
-enum { LAT_D2Q5 = 0, LAT_D3Q7 = 1 };
+enum { LAT_D2Q5 = 0, LAT_D3Q7 = 1, LAT_D3Q19 = 2 };
 
 // ------------------------------------------------------------------------------------
 // Velocity sets. Scalar sets: k = 0 at rest, then +x, -x, +y, -y (, +z, -z).
@@ -107,6 +107,21 @@ struct D3Q19 {
 };
 
 __host__ __device__ constexpr int opp(int k) { return k == 0 ? 0 : ((k & 1) ? k + 1 : k - 1); }
+
+// D3Q19 as the lattice of phi, c^A, c^B: the paper's choice for every equation (§3).
+template <> struct Scalar<LAT_D3Q19> {
+    static constexpr int Q = 19;
+    __host__ __device__ static constexpr int ex(int k) { return D3Q19::ex(k); }
+    __host__ __device__ static constexpr int ey(int k) { return D3Q19::ey(k); }
+    __host__ __device__ static constexpr int ez(int k) { return D3Q19::ez(k); }
+    __host__ __device__ static constexpr double w(int k) { return D3Q19::w(k); }
+    __host__ __device__ static constexpr double cs2() { return 1.0 / 3.0; }
+};
+
+// First plane of g, h^A, h^B in StateView::plane for a scalar lattice.
+template <int LAT> struct Planes {
+    static constexpr int G = 19, HA = 19 + Scalar<LAT>::Q, HB = 19 + 2 * Scalar<LAT>::Q;
+};
 
 // ------------------------------------------------------------------------------------
 // Storage codecs. Real is the arithmetic type (double for FP64 storage, float otherwise).

@@ -118,9 +118,9 @@ struct Node {
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
             const Slot s = ad.src(k, Scalar<LAT>::ex(k), Scalar<LAT>::ey(k), Scalar<LAT>::ez(k));
-            g[k] = load_scalar<T, SET_G, LAT, kPlaneG, 0>(st, k, s, P);
-            hA[k] = load_scalar<T, SET_H, LAT, kPlaneHA, 1>(st, k, s, P);
-            hB[k] = load_scalar<T, SET_H, LAT, kPlaneHB, 2>(st, k, s, P);
+            g[k] = load_scalar<T, SET_G, LAT, Planes<LAT>::G, 0>(st, k, s, P);
+            hA[k] = load_scalar<T, SET_H, LAT, Planes<LAT>::HA, 1>(st, k, s, P);
+            hB[k] = load_scalar<T, SET_H, LAT, Planes<LAT>::HB, 2>(st, k, s, P);
         }
     }
     template <class A>
@@ -273,7 +273,7 @@ __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, type
     const R p = interp_p(phi);
     const R muA = closure_dev(nd.dcA, p, 0, P);
     const R muB = closure_dev(nd.dcB, p, 1, P);
-    const R inv_cs2 = R(L::cs2() == 0.25 ? 4.0 : 3.0);
+    const R inv_cs2 = R(1.0 / L::cs2());
     const R omg = coef<R>(P).om_g;
     const R MA = coef<R>(P).M0[0] * (R(1) - phi) + coef<R>(P).M1[0] * phi;     // §2.3
     const R MB = coef<R>(P).M0[1] * (R(1) - phi) + coef<R>(P).M1[1] * phi;
@@ -300,14 +300,14 @@ __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, type
         const R hBpost = nd.hB[k] - omB * (nd.hB[k] - w * (muB + cBu * cu));
         const Slot s = ad.dst(k, ex, ey, ez);
         // 16-bit storage: rounding residuals of the moving populations go to the rest population
-        g0 += store_moving<T, SET_G, LAT, kPlaneG>(out, k, s, gpost, P);
-        hA0 += store_moving<T, SET_H, LAT, kPlaneHA>(out, k, s, hApost, P);
-        hB0 += store_moving<T, SET_H, LAT, kPlaneHB>(out, k, s, hBpost, P);
+        g0 += store_moving<T, SET_G, LAT, Planes<LAT>::G>(out, k, s, gpost, P);
+        hA0 += store_moving<T, SET_H, LAT, Planes<LAT>::HA>(out, k, s, hApost, P);
+        hB0 += store_moving<T, SET_H, LAT, Planes<LAT>::HB>(out, k, s, hBpost, P);
     }
     const Slot s0{self, 0};
-    store_scalar<T, SET_G, LAT, kPlaneG, 0>(out, 0, s0, g0, P);
-    store_scalar<T, SET_H, LAT, kPlaneHA, 1>(out, 0, s0, hA0, P);
-    store_scalar<T, SET_H, LAT, kPlaneHB, 2>(out, 0, s0, hB0, P);
+    store_scalar<T, SET_G, LAT, Planes<LAT>::G, 0>(out, 0, s0, g0, P);
+    store_scalar<T, SET_H, LAT, Planes<LAT>::HA, 1>(out, 0, s0, hA0, P);
+    store_scalar<T, SET_H, LAT, Planes<LAT>::HB, 2>(out, 0, s0, hB0, P);
 }
 
 // ------------------------------------------------------------------------------------
@@ -590,9 +590,9 @@ init_kernel(const DevParams P, const StateView st, const double* __restrict__ ph
         Addr<PULL> sad;
         source_of(k, L::ex(k), L::ey(k), L::ez(k), kk, sad);
         const Slot s{self, k};
-        store_scalar<T, SET_G, LAT, kPlaneG, 0>(st, k, s, R(init_value<LAT>(INIT_G, kk, sad, phi0, cA0, cB0, P)), P);
-        store_scalar<T, SET_H, LAT, kPlaneHA, 1>(st, k, s, R(init_value<LAT>(INIT_HA, kk, sad, phi0, cA0, cB0, P)), P);
-        store_scalar<T, SET_H, LAT, kPlaneHB, 2>(st, k, s, R(init_value<LAT>(INIT_HB, kk, sad, phi0, cA0, cB0, P)), P);
+        store_scalar<T, SET_G, LAT, Planes<LAT>::G, 0>(st, k, s, R(init_value<LAT>(INIT_G, kk, sad, phi0, cA0, cB0, P)), P);
+        store_scalar<T, SET_H, LAT, Planes<LAT>::HA, 1>(st, k, s, R(init_value<LAT>(INIT_HA, kk, sad, phi0, cA0, cB0, P)), P);
+        store_scalar<T, SET_H, LAT, Planes<LAT>::HB, 2>(st, k, s, R(init_value<LAT>(INIT_HB, kk, sad, phi0, cA0, cB0, P)), P);
     }
     if constexpr (FLOW) {
 #pragma unroll 1
@@ -797,17 +797,22 @@ struct Launchers {
     void launch_init_##SUFFIX(const DevParams& P, const StateView& st, int lat, bool flow, bool pull,      \
                               const double* a, const double* b, const double* c, cudaStream_t s) {        \
         if (lat == LAT_D2Q5) Launchers<T>::init<LAT_D2Q5, false>(P, st, pull, a, b, c, s);                 \
+        else if (lat == LAT_D3Q19 && flow) Launchers<T>::init<LAT_D3Q19, true>(P, st, pull, a, b, c, s);   \
+        else if (lat == LAT_D3Q19) Launchers<T>::init<LAT_D3Q19, false>(P, st, pull, a, b, c, s);          \
         else if (flow) Launchers<T>::init<LAT_D3Q7, true>(P, st, pull, a, b, c, s);                        \
         else Launchers<T>::init<LAT_D3Q7, false>(P, st, pull, a, b, c, s);                                 \
     }                                                                                                     \
     void launch_phi_##SUFFIX(const DevParams& P, const StateView& st, int lat, int mode, void* phi,       \
                              cudaStream_t s) {                                                            \
         if (lat == LAT_D2Q5) Launchers<T>::phi<LAT_D2Q5>(P, st, mode, phi, s);                             \
+        else if (lat == LAT_D3Q19) Launchers<T>::phi<LAT_D3Q19>(P, st, mode, phi, s);                      \
         else Launchers<T>::phi<LAT_D3Q7>(P, st, mode, phi, s);                                             \
     }                                                                                                     \
     void launch_step_##SUFFIX(const DevParams& P, const StateView& st, const StateView& out, int lat,     \
                               bool flow, int mode, void* phi, cudaStream_t s) {                            \
         if (lat == LAT_D2Q5) Launchers<T>::step<LAT_D2Q5, false>(P, st, out, mode, phi, s);                \
+        else if (lat == LAT_D3Q19 && flow) Launchers<T>::step<LAT_D3Q19, true>(P, st, out, mode, phi, s);  \
+        else if (lat == LAT_D3Q19) Launchers<T>::step<LAT_D3Q19, false>(P, st, out, mode, phi, s);         \
         else if (flow) Launchers<T>::step<LAT_D3Q7, true>(P, st, out, mode, phi, s);                       \
         else Launchers<T>::step<LAT_D3Q7, false>(P, st, out, mode, phi, s);                                \
     }                                                                                                     \
@@ -818,12 +823,18 @@ struct Launchers {
     void launch_fields_##SUFFIX(const DevParams& P, const StateView& st, int lat, bool flow, int mode,    \
                                 void* phi, FieldPtrs out, cudaStream_t s) {                               \
         if (lat == LAT_D2Q5) Launchers<T>::fields<LAT_D2Q5, false>(P, st, mode, phi, out, s);              \
+        else if (lat == LAT_D3Q19 && flow) Launchers<T>::fields<LAT_D3Q19, true>(P, st, mode, phi, out, s); \
+        else if (lat == LAT_D3Q19) Launchers<T>::fields<LAT_D3Q19, false>(P, st, mode, phi, out, s);       \
         else if (flow) Launchers<T>::fields<LAT_D3Q7, true>(P, st, mode, phi, out, s);                     \
         else Launchers<T>::fields<LAT_D3Q7, false>(P, st, mode, phi, out, s);                              \
     }                                                                                                     \
     void launch_reduce_##SUFFIX(const DevParams& P, const StateView& st, int lat, bool flow, int mode,    \
                                 void* phi, double* partials, int nblocks, cudaStream_t s) {               \
         if (lat == LAT_D2Q5) Launchers<T>::reduce<LAT_D2Q5, false>(P, st, mode, phi, partials, nblocks, s); \
+        else if (lat == LAT_D3Q19 && flow)                                                                \
+            Launchers<T>::reduce<LAT_D3Q19, true>(P, st, mode, phi, partials, nblocks, s);                 \
+        else if (lat == LAT_D3Q19)                                                                        \
+            Launchers<T>::reduce<LAT_D3Q19, false>(P, st, mode, phi, partials, nblocks, s);                \
         else if (flow) Launchers<T>::reduce<LAT_D3Q7, true>(P, st, mode, phi, partials, nblocks, s);       \
         else Launchers<T>::reduce<LAT_D3Q7, false>(P, st, mode, phi, partials, nblocks, s);                \
     }

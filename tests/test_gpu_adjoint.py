@@ -45,6 +45,20 @@ def test_adjoint_matches_oracle_reverse_mode(storage, tol):
     assert float((gphi - gphi_ref).abs().max() / gphi_ref.abs().max()) <= 10 * tol
 
 
+def test_adjoint_d3q19_scalar_lattice():
+    # the same reverse mode on the paper's D3Q19 lattice for phi, c^A, c^B (FP64 storage)
+    steps, K = 12, 5
+    p, phi0, cA0, cB0 = _problem((16, 16, 16), "f64", steps)
+    p = p.with_(lattice="D3Q19")
+    target = oracle_adjoint.target_fields(p, configs.THETA_TARGET, phi0, cA0, cB0, steps)
+    L_ref, gth_ref, gphi_ref = oracle_adjoint.misfit_gradient(p, configs.THETA_EVAL, phi0, cA0, cB0, steps, target)
+    L, gth, gphi = _gpu_grad(p, phi0, cA0, cB0, steps, (target["phi"], target["muA"], target["muB"]), K)
+    assert abs(L - L_ref) <= 1e-9 * abs(L_ref)
+    assert float((gth - gth_ref).abs().max() / gth_ref.abs().max()) <= 1e-9
+    gphi = gphi.double().cpu()
+    assert float((gphi - gphi_ref).abs().max() / gphi_ref.abs().max()) <= 1e-8
+
+
 def test_gradient_vanishes_at_target_parameters():
     from paper_2409_03401_gb300.adjoint import forward_fields
     steps = 30

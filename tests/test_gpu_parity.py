@@ -125,6 +125,27 @@ def test_flow_16bit_storage(storage, inplace):
     _close({k: v for k, v in errs.items() if k not in scal}, tol_u)
 
 
+# D3Q19 for phi, c^A, c^B (the paper's lattice for every equation): no flow (in-place AA),
+# flow with two copies (phi pass + per-node pull step) and flow in place (phi pass + AA step)
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("flow,inplace", [(False, False), (True, False), (True, True)])
+def test_d3q19_scalar_lattice(storage, flow, inplace):
+    if flow:
+        p, fields = configs.sedimentation(shape=(14, 18, 70), fraction=0.05, r=(3.0, 5.0), storage=storage)
+    else:
+        p, fields = configs.ripening(shape=(14, 18, 70), storage=storage)
+    q = p.with_(lattice="D3Q19", inplace=inplace)
+    _close(compare(q, fields(), 16), TOL[storage])
+
+
+def test_d3q19_scalar_lattice_fp16():
+    p, fields = configs.sedimentation(shape=(24, 24, 40), fraction=0.06, r=(4.0, 6.0), storage="f16")
+    errs = compare(p.with_(lattice="D3Q19"), fields(), 100)
+    scal, tol_s, tol_u = BARS16["f16"]
+    _close({k: v for k, v in errs.items() if k in scal}, tol_s)
+    _close({k: v for k, v in errs.items() if k not in scal}, tol_u)
+
+
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
 def test_ripening_16bit_storage(storage):
     p, fields = configs.ripening(shape=(24, 26, 40), storage=storage)
