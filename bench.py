@@ -170,11 +170,21 @@ def time_device(sim, steps, warmup, dist):
     ms = start.elapsed_time(stop)
     ms_phi, ms_step, nprof = sim.profile_end()
     if dist:
-        import torch.distributed as td
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        td.all_reduce(t, op=td.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dist, "cuda")
     return ms, ms_phi / max(nprof, 1), ms_step / max(nprof, 1)
+
+
+def max_over_ranks(value, dist, device):
+    """The largest of every rank's value (the job's time is its slowest replica's)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(world_size, nodes_per_rank, steps, ms_max):
+    """Whole-job throughput: every rank advances its own replica of nodes_per_rank nodes."""
+    return world_size * nodes_per_rank * steps / (ms_max / 1e3) / 1e6
 
 
 def time_adjoint(device, n=128, steps=200, K=100):
@@ -263,7 +273,7 @@ def gb300(args):
         ms, ms_phi, ms_step = time_device(sim, args.steps, args.warmup, dist)
     s = sim.sums()
     nodes = p.nodes
-    value = ws * nodes * args.steps / (ms / 1e3) / 1e6
+    value = job_mlups(ws, nodes, args.steps, ms)
     bytes_step = ALG_BYTES_PER_NODE["f32"] * nodes
     achieved = bytes_step / (ms_step / 1e3) / 1e9
     out = {
