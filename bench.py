@@ -335,6 +335,23 @@ def gb300(args):
                                 "roofline_frac": b19 * nodes / (vms / vs / 1e3) / 1e9 / peak}
         del v
         torch.cuda.synchronize()
+        # 2D ripening without flow on D2Q9 (§4.2.2 table): 4096^2, 27 FP32 populations in place,
+        # with the one-pass droplet count and mean radius of Eq. 67 after the timed steps
+        from workloads import configs
+        p2, f2 = configs.ripening_2d()
+        v = Simulation(p2, *f2(device=device), device=device)
+        vs = max(20, args.steps // 2)
+        vms, _, _ = time_device(v, vs, args.warmup, dist)
+        s2 = v.sums()
+        b2 = 2 * 27 * 4.0
+        n2 = p2.nodes
+        var["ripening_2d"] = {"value": ws * n2 * vs / (vms / 1e3) / 1e6, "unit": "MLUPS", "ms_per_step": vms / vs,
+                              "workload": "4096^2 D2Q9, no flow, phase fraction 0.08, FP32, in place",
+                              "alg_bytes_per_node": b2, "roofline_frac": b2 * n2 / (vms / vs / 1e3) / 1e9 / peak,
+                              "droplets_N": s2["euler"], "mean_radius": s2["interface"] / (2 * math.pi * s2["euler"]),
+                              "after_steps": args.warmup + vs}
+        del v
+        torch.cuda.synchronize()
         out["variants"] = var
 
     if not args.no_variants:

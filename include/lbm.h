@@ -39,10 +39,11 @@ typedef enum {
 } lbm_status;
 
 /* Lattice of the phi, c^A and c^B populations (the flow always uses D3Q19). LBM_D2Q5 and
- * LBM_D3Q7 are the minimal advection-diffusion sets; LBM_D3Q19 is the paper's choice for
- * every equation (§3). With flow and two state copies, LBM_D3Q7 runs the fused z-marching
- * kernel; LBM_D3Q19 runs a phi pass and a per-node pull step instead. */
-typedef enum { LBM_D2Q5 = 0, LBM_D3Q7 = 1, LBM_D3Q19 = 2 } lbm_lattice;
+ * LBM_D3Q7 are the minimal advection-diffusion sets; LBM_D3Q19 (3D) and LBM_D2Q9 (2D) are
+ * the paper's choices (§3). The 2D lattices need nz = 1 and carry no flow. With flow and two
+ * state copies, LBM_D3Q7 runs the fused z-marching kernel; LBM_D3Q19 runs a phi pass and a
+ * per-node pull step instead. */
+typedef enum { LBM_D2Q5 = 0, LBM_D3Q7 = 1, LBM_D3Q19 = 2, LBM_D2Q9 = 3 } lbm_lattice;
 
 /* Storage type of the populations. Arithmetic is FP64 for LBM_F64 and FP32 otherwise.
  * LBM_F16 / LBM_BF16 store every moving population as a 16-bit deviation from its
@@ -105,6 +106,11 @@ enum {
     LBM_RED_UMAX,        /* max |u| (Eq. 41) */
     LBM_RED_G,           /* sum of all g populations (= sum phi - sum S / 2) */
     LBM_RED_NONFINITE,   /* number of nodes with a non-finite moment */
+    LBM_RED_INTERFACE,   /* sum (4/W) phi (1 - phi): interface length (2D) or area (3D); Eq. 67 gives
+                          * the mean droplet radius <R> = this / (2 pi N) in 2D */
+    LBM_RED_EULER,       /* 2D lattices: Euler characteristic of {phi >= 1/2} with 8-connected
+                          * droplets (Gray's 2x2 bit quads, one pass), i.e. the droplet count N
+                          * when no droplet has a hole (§4.2.2 measures N this way); 0 in 3D */
     LBM_NRED
 };
 

@@ -10,14 +10,14 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblbm_gb300.so")
 
 LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_UNSTABLE, LBM_ERR_STATE = 0, -1, -2, -3, -4
-LBM_D2Q5, LBM_D3Q7, LBM_D3Q19 = 0, 1, 2
+LBM_D2Q5, LBM_D3Q7, LBM_D3Q19, LBM_D2Q9 = 0, 1, 2, 3
 LBM_F64, LBM_F32, LBM_F16, LBM_BF16 = 0, 1, 2, 3
 STORAGE = {"f64": LBM_F64, "f32": LBM_F32, "f16": LBM_F16, "bf16": LBM_BF16}
-LATTICE = {"D2Q5": LBM_D2Q5, "D3Q7": LBM_D3Q7, "D3Q19": LBM_D3Q19}
+LATTICE = {"D2Q5": LBM_D2Q5, "D3Q7": LBM_D3Q7, "D3Q19": LBM_D3Q19, "D2Q9": LBM_D2Q9}
 LBM_BGK, LBM_TRT = 0, 1
 COLLISION = {"BGK": LBM_BGK, "TRT": LBM_TRT}
 FIELDS = ("phi", "muA", "muB", "cA", "cB", "p", "ux", "uy", "uz", "S")
-REDUCTIONS = ("phi", "cA", "cB", "p", "S", "umax", "g", "nonfinite")
+REDUCTIONS = ("phi", "cA", "cB", "p", "S", "umax", "g", "nonfinite", "interface", "euler")
 NFIELDS = len(FIELDS)
 NRED = len(REDUCTIONS)
 

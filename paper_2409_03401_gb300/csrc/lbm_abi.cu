@@ -19,7 +19,10 @@ constexpr int kRedBlocks = 1216;   // 152 SMs x 8 blocks of 256 threads
 
 long long round_up(long long v, long long a) { return (v + a - 1) / a * a; }
 
-int scalar_q(int lattice) { return lattice == LBM_D2Q5 ? 5 : (lattice == LBM_D3Q19 ? 19 : 7); }
+int scalar_q(int lattice) {
+    return lattice == LBM_D2Q5 ? 5 : (lattice == LBM_D3Q19 ? 19 : (lattice == LBM_D2Q9 ? 9 : 7));
+}
+bool two_d(int lattice) { return lattice == LBM_D2Q5 || lattice == LBM_D2Q9; }
 // the fused z-marching flow kernel is written for D3Q7 scalar sets
 bool fused_flow(const lbm_params* p) { return p->lattice == LBM_D3Q7; }
 size_t storage_size(int s) { return s == LBM_F64 ? 8 : (s == LBM_F32 ? 4 : 2); }
@@ -41,11 +44,11 @@ const char* check_params(const lbm_params* p) {
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) return "lattice extents must be >= 1";
     if (p->ny > 65535 || p->nz > 65535) return "ny and nz must be <= 65535";
     if ((long long)p->nx * p->ny * p->nz >= (1LL << 31)) return "nx*ny*nz must be < 2^31";
-    if (p->lattice != LBM_D2Q5 && p->lattice != LBM_D3Q7 && p->lattice != LBM_D3Q19)
-        return "lattice must be LBM_D2Q5, LBM_D3Q7 or LBM_D3Q19";
-    if (p->lattice == LBM_D2Q5 && p->nz != 1) return "LBM_D2Q5 needs nz == 1";
+    if (p->lattice != LBM_D2Q5 && p->lattice != LBM_D3Q7 && p->lattice != LBM_D3Q19 && p->lattice != LBM_D2Q9)
+        return "lattice must be LBM_D2Q5, LBM_D3Q7, LBM_D3Q19 or LBM_D2Q9";
+    if (two_d(p->lattice) && p->nz != 1) return "the 2D lattices (LBM_D2Q5, LBM_D2Q9) need nz == 1";
     if (p->flow != 0 && p->flow != 1) return "flow must be 0 or 1";
-    if (p->flow && p->lattice == LBM_D2Q5) return "flow needs a 3D scalar lattice (LBM_D3Q7 or LBM_D3Q19)";
+    if (p->flow && two_d(p->lattice)) return "flow needs a 3D scalar lattice (LBM_D3Q7 or LBM_D3Q19)";
     if (p->storage < LBM_F64 || p->storage > LBM_BF16) return "storage must be one of lbm_storage";
     if (p->inplace != 0 && p->inplace != 1) return "inplace must be 0 or 1";
     if (!(p->W > 0)) return "W must be > 0";
@@ -78,7 +81,8 @@ Layout layout_of(const lbm_params* p) {
     L.state = L.copy * (L.two ? 2 : 1);
     const size_t real = p->storage == LBM_F64 ? 8 : 4;
     size_t w = 0;
-    L.off_phi = w;      w += p->flow ? round_up((size_t)L.plane * real, kAlign) : 0;
+    // the phi field: read by the capillary stencil (flow) and by the 2D Euler count
+    L.off_phi = w;      w += (p->flow || two_d(p->lattice)) ? round_up((size_t)L.plane * real, kAlign) : 0;
     L.off_partials = w; w += round_up((size_t)kRedBlocks * LBM_NRED * sizeof(double), kAlign);
     L.off_out = w;      w += round_up(LBM_NRED * sizeof(double), kAlign);
     L.work = w;

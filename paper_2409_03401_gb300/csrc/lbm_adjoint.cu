@@ -352,10 +352,12 @@ void adjoint_init_T(const DevParams& P, const double* phi0, const double* cA0, c
     do {                                                                                        \
         if (STORAGE == 0) {                                                                     \
             if (LAT == LAT_D2Q5) FN<double, LAT_D2Q5>(__VA_ARGS__);                             \
+            else if (LAT == LAT_D2Q9) FN<double, LAT_D2Q9>(__VA_ARGS__);                        \
             else if (LAT == LAT_D3Q19) FN<double, LAT_D3Q19>(__VA_ARGS__);                      \
             else FN<double, LAT_D3Q7>(__VA_ARGS__);                                             \
         } else {                                                                                \
             if (LAT == LAT_D2Q5) FN<float, LAT_D2Q5>(__VA_ARGS__);                              \
+            else if (LAT == LAT_D2Q9) FN<float, LAT_D2Q9>(__VA_ARGS__);                         \
             else if (LAT == LAT_D3Q19) FN<float, LAT_D3Q19>(__VA_ARGS__);                       \
             else FN<float, LAT_D3Q7>(__VA_ARGS__);                                              \
         }                                                                                       \

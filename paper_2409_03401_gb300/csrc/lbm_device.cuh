@@ -61,7 +61,7 @@ struct StateView {
     void* plane[kPlanes];
 };
 
-enum { LAT_D2Q5 = 0, LAT_D3Q7 = 1, LAT_D3Q19 = 2 };
+enum { LAT_D2Q5 = 0, LAT_D3Q7 = 1, LAT_D3Q19 = 2, LAT_D2Q9 = 3 };
 
 // ------------------------------------------------------------------------------------
 // Velocity sets. Scalar sets: k = 0 at rest, then +x, -x, +y, -y (, +z, -z).
@@ -115,6 +115,23 @@ template <> struct Scalar<LAT_D3Q19> {
     __host__ __device__ static constexpr int ey(int k) { return D3Q19::ey(k); }
     __host__ __device__ static constexpr int ez(int k) { return D3Q19::ez(k); }
     __host__ __device__ static constexpr double w(int k) { return D3Q19::w(k); }
+    __host__ __device__ static constexpr double cs2() { return 1.0 / 3.0; }
+};
+
+// D2Q9 as the lattice of phi, c^A, c^B in 2D (the paper's choice in 2D, §3): rest, the four
+// axis directions, then the diagonals, opposite pairs adjacent as in every set here.
+template <> struct Scalar<LAT_D2Q9> {
+    static constexpr int Q = 9;
+    __host__ __device__ static constexpr int ex(int k) {
+        return (k == 1 || k == 5 || k == 7) ? 1 : ((k == 2 || k == 6 || k == 8) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int ey(int k) {
+        return (k == 3 || k == 5 || k == 8) ? 1 : ((k == 4 || k == 6 || k == 7) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int ez(int) { return 0; }
+    __host__ __device__ static constexpr double w(int k) {
+        return k == 0 ? 4.0 / 9.0 : (k <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+    }
     __host__ __device__ static constexpr double cs2() { return 1.0 / 3.0; }
 };
 

@@ -647,6 +647,31 @@ fields_kernel(const DevParams P, const StateView st, const typename RealOf<T>::t
         if (out.p[i]) static_cast<R*>(out.p[i])[ad.self] = vals[i];
 }
 
+template <int LAT> constexpr bool kTwoD = LAT == LAT_D2Q5 || LAT == LAT_D2Q9;
+
+// Euler characteristic of the 8-connected set {phi >= 1/2} of a 2D lattice by Gray's bit
+// quads: over all 2x2 windows, chi = (n1 - n3 - 2 nd) / 4 with n1 (n3) the windows holding
+// one (three) set pixels and nd those holding a diagonal pair. Node (x, y) owns the window
+// spanning x..x+1, y..y+1 (periodic wrap; outside an x wall counts as empty, and the node
+// at x = 0 also owns the window reaching out to x = -1). Returns its share of chi.
+template <class R>
+__device__ __forceinline__ double euler_quads(const R* __restrict__ phi, int x, int y, const DevParams& P) {
+    const int yp = y + 1 < P.ny ? y + 1 : 0;
+    auto on = [&](int xx, int yy) {
+        return xx >= 0 && xx < P.nx && phi[yy * P.nx + xx] >= R(0.5);
+    };
+    auto window = [&](int x0, int x1) {
+        const int a = on(x0, y), b = on(x1, y), c = on(x0, yp), d = on(x1, yp);
+        const int n = a + b + c + d;
+        const int diag = (n == 2 && a == d) ? 1 : 0;
+        return double((n == 1) - (n == 3) - 2 * diag);
+    };
+    const int xp = x + 1 < P.nx ? x + 1 : (P.wall_x ? P.nx : 0);
+    double q = window(x, xp);
+    if (P.wall_x && x == 0) q += window(-1, 0);
+    return 0.25 * q;
+}
+
 // FP64 block partials of the global diagnostics (grid-stride over nodes).
 template <class T, int LAT, bool FLOW, int MODE>
 __global__ void __launch_bounds__(256)
@@ -689,6 +714,8 @@ reduce_kernel(const DevParams P, const StateView st, const typename RealOf<T>::t
         acc[5] = fmax(acc[5], isfinite(umag) ? umag : 0.0);
         acc[6] += double(nd.phit);
         acc[7] += finite ? 0.0 : 1.0;
+        acc[8] += 4.0 / P.W * double(phi) * (1.0 - double(phi));          // Eq. 67 integrand
+        if constexpr (kTwoD<LAT>) acc[9] += euler_quads(phi_field, x, y, P);
     }
     // block reduction: warp shuffles, then one warp over the warp results
     __shared__ double sm[LBM_NRED_DEV][32];
@@ -784,7 +811,7 @@ struct Launchers {
     static void reduce(const DevParams& P, const StateView& st, int mode, void* phi_work, double* partials,
                        int nblocks, cudaStream_t s) {
         R* phi = static_cast<R*>(phi_work);
-        if constexpr (FLOW) {
+        if constexpr (FLOW || kTwoD<LAT>) {
             int bx; const dim3 grid = node_grid(P, bx);
             LBM_MODE_SWITCH(mode, phi_kernel<T, LAT, M><<<grid, bx, 0, s>>>(P, st, phi));
         }
@@ -797,6 +824,7 @@ struct Launchers {
     void launch_init_##SUFFIX(const DevParams& P, const StateView& st, int lat, bool flow, bool pull,      \
                               const double* a, const double* b, const double* c, cudaStream_t s) {        \
         if (lat == LAT_D2Q5) Launchers<T>::init<LAT_D2Q5, false>(P, st, pull, a, b, c, s);                 \
+        else if (lat == LAT_D2Q9) Launchers<T>::init<LAT_D2Q9, false>(P, st, pull, a, b, c, s);            \
         else if (lat == LAT_D3Q19 && flow) Launchers<T>::init<LAT_D3Q19, true>(P, st, pull, a, b, c, s);   \
         else if (lat == LAT_D3Q19) Launchers<T>::init<LAT_D3Q19, false>(P, st, pull, a, b, c, s);          \
         else if (flow) Launchers<T>::init<LAT_D3Q7, true>(P, st, pull, a, b, c, s);                        \
@@ -805,12 +833,14 @@ struct Launchers {
     void launch_phi_##SUFFIX(const DevParams& P, const StateView& st, int lat, int mode, void* phi,       \
                              cudaStream_t s) {                                                            \
         if (lat == LAT_D2Q5) Launchers<T>::phi<LAT_D2Q5>(P, st, mode, phi, s);                             \
+        else if (lat == LAT_D2Q9) Launchers<T>::phi<LAT_D2Q9>(P, st, mode, phi, s);                        \
         else if (lat == LAT_D3Q19) Launchers<T>::phi<LAT_D3Q19>(P, st, mode, phi, s);                      \
         else Launchers<T>::phi<LAT_D3Q7>(P, st, mode, phi, s);                                             \
     }                                                                                                     \
     void launch_step_##SUFFIX(const DevParams& P, const StateView& st, const StateView& out, int lat,     \
                               bool flow, int mode, void* phi, cudaStream_t s) {                            \
         if (lat == LAT_D2Q5) Launchers<T>::step<LAT_D2Q5, false>(P, st, out, mode, phi, s);                \
+        else if (lat == LAT_D2Q9) Launchers<T>::step<LAT_D2Q9, false>(P, st, out, mode, phi, s);           \
         else if (lat == LAT_D3Q19 && flow) Launchers<T>::step<LAT_D3Q19, true>(P, st, out, mode, phi, s);  \
         else if (lat == LAT_D3Q19) Launchers<T>::step<LAT_D3Q19, false>(P, st, out, mode, phi, s);         \
         else if (flow) Launchers<T>::step<LAT_D3Q7, true>(P, st, out, mode, phi, s);                       \
@@ -823,6 +853,7 @@ struct Launchers {
     void launch_fields_##SUFFIX(const DevParams& P, const StateView& st, int lat, bool flow, int mode,    \
                                 void* phi, FieldPtrs out, cudaStream_t s) {                               \
         if (lat == LAT_D2Q5) Launchers<T>::fields<LAT_D2Q5, false>(P, st, mode, phi, out, s);              \
+        else if (lat == LAT_D2Q9) Launchers<T>::fields<LAT_D2Q9, false>(P, st, mode, phi, out, s);         \
         else if (lat == LAT_D3Q19 && flow) Launchers<T>::fields<LAT_D3Q19, true>(P, st, mode, phi, out, s); \
         else if (lat == LAT_D3Q19) Launchers<T>::fields<LAT_D3Q19, false>(P, st, mode, phi, out, s);       \
         else if (flow) Launchers<T>::fields<LAT_D3Q7, true>(P, st, mode, phi, out, s);                     \
@@ -831,6 +862,7 @@ struct Launchers {
     void launch_reduce_##SUFFIX(const DevParams& P, const StateView& st, int lat, bool flow, int mode,    \
                                 void* phi, double* partials, int nblocks, cudaStream_t s) {               \
         if (lat == LAT_D2Q5) Launchers<T>::reduce<LAT_D2Q5, false>(P, st, mode, phi, partials, nblocks, s); \
+        else if (lat == LAT_D2Q9) Launchers<T>::reduce<LAT_D2Q9, false>(P, st, mode, phi, partials, nblocks, s); \
         else if (lat == LAT_D3Q19 && flow)                                                                \
             Launchers<T>::reduce<LAT_D3Q19, true>(P, st, mode, phi, partials, nblocks, s);                 \
         else if (lat == LAT_D3Q19)                                                                        \

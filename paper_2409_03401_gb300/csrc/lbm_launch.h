@@ -7,7 +7,7 @@
 #include "lbm_device.cuh"
 
 #define LBM_NFIELDS_DEV 10
-#define LBM_NRED_DEV 8
+#define LBM_NRED_DEV 10
 
 namespace lbm {
 

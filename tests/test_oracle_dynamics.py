@@ -62,10 +62,13 @@ def test_bulk_phase_one_fixed_point():
         assert float((v - before[k]).abs().max()) < 1e-14, k
 
 
-@pytest.mark.parametrize("case", ["flow_walls", "periodic", "couple_walls", "flow_walls_d3q19"])
+@pytest.mark.parametrize("case", ["flow_walls", "periodic", "couple_walls", "flow_walls_d3q19", "periodic_d2q9"])
 def test_conservation_and_phi_budget(case):
     if case == "flow_walls":
         p, fields = configs.sedimentation(shape=(16, 16, 18), fraction=0.04, r=(3.0, 4.5))
+    elif case == "periodic_d2q9":
+        p, fields = configs.ripening(shape=(1, 40, 48))
+        p = p.with_(lattice="D2Q9")
     elif case == "flow_walls_d3q19":
         p, fields = configs.sedimentation(shape=(16, 16, 18), fraction=0.04, r=(3.0, 4.5))
         p = p.with_(lattice="D3Q19")
@@ -87,7 +90,7 @@ def test_conservation_and_phi_budget(case):
         s = s1
 
 
-@pytest.mark.parametrize("lattice", ["D3Q7", "D2Q5", "D3Q19"])
+@pytest.mark.parametrize("lattice", ["D3Q7", "D2Q5", "D3Q19", "D2Q9"])
 def test_mode_decay_rates(lattice):
     n = 64
     k = 2 * math.pi / n
@@ -184,7 +187,7 @@ def test_trt_with_equal_rates_is_bgk():
     assert float((runs[0].f - o.f).abs().max()) > 1e-9
 
 
-@pytest.mark.parametrize("lattice", ["D2Q5", "D3Q7", "D3Q19"])
+@pytest.mark.parametrize("lattice", ["D2Q5", "D3Q7", "D3Q19", "D2Q9"])
 @pytest.mark.parametrize("W,tol", [(3.0, 1e-2), (6.0, 3e-3)])
 def test_flat_interface_is_stationary(lattice, W, tol):
     # a slab of phase 1 with mu = 0 keeps the tanh profile of Eq. 13; the residual gap is the

@@ -162,19 +162,22 @@ def _random_node_state(seed, flow=True):
     return phi, c, mu, u, F, S, ph
 
 
-@pytest.mark.parametrize("lattice", ["D3Q7", "D3Q19"])
+@pytest.mark.parametrize("lattice", ["D3Q7", "D3Q19", "D2Q9"])
 def test_equilibrium_moment_identities(lattice):
-    p = LBMParams(nx=3, ny=2, nz=1, lattice=lattice, flow=True)
+    p = LBMParams(nx=3, ny=2, nz=1, lattice=lattice, flow=lattice != "D2Q9")
     o = OracleLBM(p)
     phi, c, mu, u, F, S, ph = _random_node_state(1)
     ls = L.BY_NAME[lattice]
     es = ls.e_tensor()
+    dims = 2 if lattice == "D2Q9" else 3
+    if dims == 2:
+        u[2] = torch.zeros_like(u[2])                   # planar motion on a 2D lattice
     # Eq. 51: sum h = c, sum h e = c u, sum h e e = c_s^2 mu I
     h = o._h_eq(c, mu, u)
     assert torch.allclose(h.sum(0), c, rtol=0, atol=1e-15)
-    for a in range(3):
+    for a in range(dims):
         assert torch.allclose((h * es[:, a].reshape(-1, 1, 1, 1)).sum(0), c * u[a], rtol=0, atol=1e-15)
-        for b in range(3):
+        for b in range(dims):
             mom = (h * (es[:, a] * es[:, b]).reshape(-1, 1, 1, 1)).sum(0)
             want = ls.cs2 * mu if a == b else torch.zeros_like(mu)
             assert torch.allclose(mom, want, rtol=0, atol=1e-15)
@@ -183,7 +186,7 @@ def test_equilibrium_moment_identities(lattice):
     cu = torch.stack([sum(ls.e[k][a] * u[a] for a in range(3)) for k in range(ls.Q)])
     geq = w * phi * (1 + cu / ls.cs2) - 0.5 * w * S
     assert torch.allclose(geq.sum(0), phi - S / 2, rtol=0, atol=1e-15)
-    for a in range(3):
+    for a in range(dims):
         assert torch.allclose((geq * es[:, a].reshape(-1, 1, 1, 1)).sum(0), phi * u[a], rtol=0, atol=1e-15)
     # Eqs. 37-41: sum F_k = 0, sum F_k c_k = c_s^2 F exactly on D3Q19, sum f^eq = p_h,
     # and the velocity moment of f^eq returns u

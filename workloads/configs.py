@@ -1,4 +1,4 @@
-"""The five synthetic workloads of the coupled step, in lattice units.
+"""The six synthetic workloads of the coupled step, in lattice units.
 
 Each builder returns ``(params, fields)`` where ``fields(device)`` yields the
 initial (phi, c^A, c^B) as float64 tensors of shape (nz, ny, nx). Sizes can be
@@ -25,6 +25,8 @@ Parameter choices where the paper or the workload description is silent:
   cancel the kinetic coefficient of Eq. 27 at this M_phi; at lambda = 60 the
   kinetic coefficient is 0.094 and the interface follows x_I ~ sqrt(t).
 """
+import math
+
 from .params import LBMParams
 from .droplets import place_droplets, phi_field, composition_fields, planar_couple
 
@@ -44,19 +46,20 @@ def diffusion_couple(nx=512, ny=8, storage="f64"):
     return p, fields
 
 
-def _droplet_workload(p, fraction, r_min, r_max, seed):
+def _droplet_workload(p, fraction, r_min, r_max, seed, sample_volume=False, supersaturation=SUPERSATURATION):
     walls = (p.wall_x, False, p.wall_z)
     cache = {}
 
     def geometry():
         if "g" not in cache:
-            cache["g"] = place_droplets(p.shape, fraction, r_min, r_max, p.W, seed, walls=walls)
+            cache["g"] = place_droplets(p.shape, fraction, r_min, r_max, p.W, seed, walls=walls,
+                                        sample_volume=sample_volume)
         return cache["g"]
 
     def fields(device="cpu", z_range=None):
         centres, radii = geometry()
         phi = phi_field(p.shape, centres, radii, p.W, walls=walls, device=device, z_range=z_range)
-        cA, cB = composition_fields(phi, p.c_eq, SUPERSATURATION)
+        cA, cB = composition_fields(phi, p.c_eq, supersaturation)
         return phi, cA, cB
     fields.geometry = geometry
     return fields
@@ -74,6 +77,26 @@ def sedimentation(n=512, storage="f32", shape=None, seed=3, fraction=0.2, r=(6.0
     nz, ny, nx = shape or (n, n, n)
     p = LBMParams(nx=nx, ny=ny, nz=nz, lattice="D3Q7", flow=True, storage=storage, wall_z=True)
     return p, _droplet_workload(p, fraction, r[0], r[1], seed)
+
+
+# 2D ripening without flow (§4.2.2 table, D2Q9): the table's collision times tau_g = 0.8776,
+# tau_h^A = 0.8146, tau_h^B = 0.7517 are classic BGK times, so M = (tau - 1/2) c_s^2 with
+# c_s^2 = 1/3; the matrix composition c_g = 0.31 is 10 % of the gap above c_0^eq; droplet
+# areas uniform in (1.02 +- 0.957) x 10^-4 L^2 at dx = 4.882 x 10^-4 L, i.e. 26.5 to 829.5
+# nodes^2 (radii 2.90 to 16.25 nodes), at phase fraction 0.08.
+RIPENING_2D_M = ((0.8146 - 0.5) / 3.0, (0.7517 - 0.5) / 3.0)
+RIPENING_2D_M_PHI = (0.8776 - 0.5) / 3.0
+RIPENING_2D_R = (math.sqrt(26.5 / math.pi), math.sqrt(829.5 / math.pi))
+
+
+def ripening_2d(n=4096, storage="f32", shape=None, seed=6):
+    """2D Ostwald ripening without flow, periodic, on D2Q9 (the paper's 4096^2 run)."""
+    nz, ny, nx = shape or (1, n, n)
+    p = LBMParams(nx=nx, ny=ny, nz=nz, lattice="D2Q9", flow=False, storage=storage, W=3.0, lam=155.95,
+                  M_phi=RIPENING_2D_M_PHI, c_eq=((0.3, 0.3), (0.4, 0.4)),
+                  M=(RIPENING_2D_M, RIPENING_2D_M))
+    return p, _droplet_workload(p, 0.08, RIPENING_2D_R[0], RIPENING_2D_R[1], seed, sample_volume=True,
+                                supersaturation=0.1)
 
 
 def drift(n=384, storage="f32", shape=None, seed=4):
@@ -101,6 +124,7 @@ def adjoint_problem(n=128, storage="f32", shape=None, seed=5, theta=THETA_EVAL):
 CONFIGS = {
     "couple": diffusion_couple,
     "ripening": ripening,
+    "ripening_2d": ripening_2d,
     "sedimentation": sedimentation,
     "drift": drift,
     "adjoint": adjoint_problem,

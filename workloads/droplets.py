@@ -3,7 +3,9 @@
 Recipe (input generation only, shared by the oracle tests and the CUDA path):
 
 * ``place_droplets`` - random sequential addition driven by SplitMix64: a
-  centre uniform in the box and a radius uniform in [r_min, r_max]; a
+  centre uniform in the box and a radius uniform in [r_min, r_max] (or, with
+  ``sample_volume``, a disc area / sphere volume uniform between those of
+  r_min and r_max, as the paper samples droplet volumes, §4.2.1); a
   candidate is rejected when it comes closer than r_i + r_j + W to a previous
   droplet (minimum-image distance along periodic axes) or, along a walled axis,
   when its surface comes closer than W/2 to the wall plane (walls at -1/2 and
@@ -27,7 +29,7 @@ from .rng import SplitMix64
 
 
 def place_droplets(shape, fraction, r_min, r_max, W, seed, walls=(False, False, False),
-                   max_attempts=1_000_000):
+                   max_attempts=1_000_000, sample_volume=False):
     """Return (centres [N, 3] as (x, y, z), radii [N]) as float64 numpy arrays.
 
     ``shape`` is (nz, ny, nx); ``walls`` flags the (x, y, z) axes bounded by
@@ -58,7 +60,13 @@ def place_droplets(shape, fraction, r_min, r_max, W, seed, walls=(False, False, 
                 f"droplet placement gave up after {max_attempts} attempts at fraction "
                 f"{covered / box:.4f} < {fraction}")
         c = (rng.uniform() * nx, rng.uniform() * ny, 0.0 if two_d else rng.uniform() * nz)
-        r = rng.uniform_range(r_min, r_max)
+        if sample_volume:                                    # disc area (2D) or sphere volume
+            if two_d:
+                r = math.sqrt(rng.uniform_range(r_min * r_min, r_max * r_max))
+            else:
+                r = rng.uniform_range(r_min ** 3, r_max ** 3) ** (1.0 / 3.0)
+        else:
+            r = rng.uniform_range(r_min, r_max)
         ok = True
         for ax in range(dims):
             if walls[ax]:

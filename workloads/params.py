@@ -15,7 +15,7 @@ or the two-relaxation-time operator it names as an alternative (§3).
 from dataclasses import dataclass, field, asdict, replace
 from typing import Tuple
 
-LATTICES = ("D2Q5", "D3Q7", "D3Q19")
+LATTICES = ("D2Q5", "D3Q7", "D3Q19", "D2Q9")
 COLLISIONS = ("BGK", "TRT")
 STORAGES = ("f64", "f32", "f16", "bf16")
 
@@ -51,13 +51,13 @@ class LBMParams:
             raise ValueError(f"storage must be one of {STORAGES}")
         if min(self.nx, self.ny, self.nz) < 1:
             raise ValueError("lattice extents must be >= 1")
-        if self.lattice == "D2Q5" and self.nz != 1:
-            raise ValueError("D2Q5 needs nz == 1")
+        if self.lattice in ("D2Q5", "D2Q9") and self.nz != 1:
+            raise ValueError("the 2D lattices need nz == 1")
         if self.collision not in COLLISIONS:
             raise ValueError(f"collision must be one of {COLLISIONS}")
         if not self.trt_magic > 0:
             raise ValueError("trt_magic must be > 0")
-        if self.flow and self.lattice == "D2Q5":
+        if self.flow and self.lattice in ("D2Q5", "D2Q9"):
             raise ValueError("flow is implemented on 3D lattices (D3Q19 flow + D3Q7 or D3Q19 scalars)")
 
     @property
