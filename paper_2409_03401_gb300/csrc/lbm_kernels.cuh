@@ -528,35 +528,11 @@ fused_flow_kernel(const DevParams P, const StateView src, const StateView dst, i
 }
 
 // ------------------------------------------------------------------------------------
-// Initial populations at rest, computed in FP64 then stored. MODE AA_EVEN writes the
-// incoming populations in their own slots (time 0 of the AA pattern); MODE PULL writes
-// what a pull gather must find: slot k of node y holds the initial population k of node
-// y + e_k, or, beyond a wall, the initial population opp(k) of y itself.
-enum { INIT_G = 0, INIT_HA = 1, INIT_HB = 2, INIT_F = 3 };
-
-template <int LAT>
-__device__ __forceinline__ double init_value(int set, int k, const Addr<PULL>& ad,
-                                             const double* __restrict__ phi0, const double* __restrict__ cA0,
-                                             const double* __restrict__ cB0, const DevParams& P) {
-    const int node = ad.self;
-    const double ph = phi0[node];
-    if (set == INIT_F) {
-        double gx, gy, gz, lap;
-        stencil([&](int dx, int dy, int dz) { return ad.phi(phi0, dx, dy, dz); }, ph, gx, gy, gz, lap);
-        const double br = P.sw15 * (dwell_d(ph) * P.inv_W2 - lap);
-        const double Fx = br * gx + ph * P.g[0], Fy = br * gy + ph * P.g[1], Fz = br * gz + ph * P.g[2];
-        const double w = D3Q19::w(k);
-        return -0.5 * w * (D3Q19::ex(k) * Fx + D3Q19::ey(k) * Fy + D3Q19::ez(k) * Fz);   // Eqs. 37-39
-    }
-    const double pp = interp_p(ph);
-    const double dA = cA0[node] - P.c0[0], dB = cB0[node] - P.c0[1];
-    const double muA = closure_dev(dA, pp, 0, P), muB = closure_dev(dB, pp, 1, P);
-    const double w = Scalar<LAT>::w(k);
-    if (set == INIT_G) return w * ph - 0.5 * w * source(ph, muA, muB, P);             // Eq. 47, u = 0
-    const double d = set == INIT_HA ? dA : dB, mu = set == INIT_HA ? muA : muB;       // Eq. 51, u = 0
-    return k == 0 ? d - (1.0 - w) * mu : w * mu;                                      // h_0 shifted by c_0^eq
-}
-
+// Initial populations at rest, computed in FP64 then stored (Eqs. 47, 51 and 37-39 at
+// u = 0, p_h = 0). Each node evaluates its phi_0-derived quantities once and stores its
+// population k in the slot its own first gather of k will read (Addr<MODE>::src): its own
+// slot k for AA_EVEN; for PULL slot k of node x - e_k, or, when that lies beyond a wall,
+// its own slot opp(k). Every slot has exactly one writer.
 template <class T, int LAT, bool FLOW, int MODE>
 __global__ void __launch_bounds__(kBlockX)
 init_kernel(const DevParams P, const StateView st, const double* __restrict__ phi0,
@@ -566,43 +542,36 @@ init_kernel(const DevParams P, const StateView st, const double* __restrict__ ph
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     if (x >= P.nx) return;
-    const int self = node_of(x, y, z, P);
-    Nbr nb;
-    nb.init(x, y, z, P);
-    // which node's initial population (and which index) slot k of this node holds
-    auto source_of = [&](int k, int ex, int ey, int ez, int& kk, Addr<PULL>& sad) {
-        sad.nb = nb;
-        sad.self = self;
-        kk = k;
-        if (MODE == PULL && k != 0) {
-            int q;
-            if (nb.at(ex, ey, ez, self, q)) {
-                sad.self = q;
-                sad.nb.init(nb.c[0][ex + 1], nb.c[1][ey + 1], nb.c[2][ez + 1], P);
-            } else {
-                kk = opp(k);
-            }
-        }
-    };
-#pragma unroll 1
+    Addr<MODE> ad;
+    ad.self = node_of(x, y, z, P);
+    ad.nb.init(x, y, z, P);
+    const double ph = phi0[ad.self];
+    const double pp = interp_p(ph);
+    const double dA = cA0[ad.self] - P.c0[0], dB = cB0[ad.self] - P.c0[1];
+    const double muA = closure_dev(dA, pp, 0, P), muB = closure_dev(dB, pp, 1, P);
+    const double S = source(ph, muA, muB, P);
+#pragma unroll
     for (int k = 0; k < L::Q; ++k) {
-        int kk;
-        Addr<PULL> sad;
-        source_of(k, L::ex(k), L::ey(k), L::ez(k), kk, sad);
-        const Slot s{self, k};
-        store_scalar<T, SET_G, LAT, Planes<LAT>::G, 0>(st, k, s, R(init_value<LAT>(INIT_G, kk, sad, phi0, cA0, cB0, P)), P);
-        store_scalar<T, SET_H, LAT, Planes<LAT>::HA, 1>(st, k, s, R(init_value<LAT>(INIT_HA, kk, sad, phi0, cA0, cB0, P)), P);
-        store_scalar<T, SET_H, LAT, Planes<LAT>::HB, 2>(st, k, s, R(init_value<LAT>(INIT_HB, kk, sad, phi0, cA0, cB0, P)), P);
+        const double w = L::w(k);
+        const Slot s = ad.src(k, L::ex(k), L::ey(k), L::ez(k));
+        store_scalar<T, SET_G, LAT, Planes<LAT>::G, 0>(st, k, s, R(w * ph - 0.5 * w * S), P);   // Eq. 47
+        const double hA = k == 0 ? dA - (1.0 - w) * muA : w * muA;                         // Eq. 51,
+        const double hB = k == 0 ? dB - (1.0 - w) * muB : w * muB;                         // h_0 shifted
+        store_scalar<T, SET_H, LAT, Planes<LAT>::HA, 1>(st, k, s, R(hA), P);
+        store_scalar<T, SET_H, LAT, Planes<LAT>::HB, 2>(st, k, s, R(hB), P);
     }
     if constexpr (FLOW) {
-#pragma unroll 1
+        double gx, gy, gz, lap;
+        stencil([&](int dx, int dy, int dz) { return ad.phi(phi0, dx, dy, dz); }, ph, gx, gy, gz, lap);
+        const double br = P.sw15 * (dwell_d(ph) * P.inv_W2 - lap);
+        const double Fx = br * gx + ph * P.g[0], Fy = br * gy + ph * P.g[1], Fz = br * gz + ph * P.g[2];
+#pragma unroll
         for (int k = 0; k < 19; ++k) {
-            int kk;
-            Addr<PULL> sad;
-            source_of(k, D3Q19::ex(k), D3Q19::ey(k), D3Q19::ez(k), kk, sad);
-            const R v = R(init_value<LAT>(INIT_F, kk, sad, phi0, cA0, cB0, P));
-            if (is16<T>() && k == 0) st.rest[3 * P.plane + self] = float(v);
-            else Codec<T>::template store<SET_F>(element<T, 0>(st, k, Slot{self, k}), v, D3Q19::w(k), P);
+            const int ex = D3Q19::ex(k), ey = D3Q19::ey(k), ez = D3Q19::ez(k);
+            const R v = R(-0.5 * D3Q19::w(k) * (ex * Fx + ey * Fy + ez * Fz));          // Eqs. 37-39
+            const Slot s = ad.src(k, ex, ey, ez);
+            if (is16<T>() && k == 0) st.rest[3 * P.plane + s.node] = float(v);
+            else Codec<T>::template store<SET_F>(element<T, 0>(st, k, s), v, D3Q19::w(k), P);
         }
     }
 }
