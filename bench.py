@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--cpu-sample-steps", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle leg (profiling runs)")
     ap.add_argument("--adjoint-only", action="store_true", help="time only the adjoint variant (profiling runs)")
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
+                    help="population storage of the main line (profiling runs; the headline is f32)")
     ap.add_argument("--adjoint-steps", type=int, default=200)
     ap.add_argument("--adjoint-k", type=int, default=100, help="checkpoint interval of the adjoint variant")
     return ap.parse_args()
@@ -266,7 +268,7 @@ def gb300(args):
     device = torch.device("cuda", local)
     from paper_2409_03401_gb300 import Simulation
 
-    p, fields_fn, init = make_workload(args.n, device)
+    p, fields_fn, init = make_workload(args.n, device, args.storage)
     sim = Simulation(p, *init, device=device)
     peak, peak_kind = peaks()
     with ClockSampler(local) as clk:
@@ -274,20 +276,22 @@ def gb300(args):
     s = sim.sums()
     nodes = p.nodes
     value = job_mlups(ws, nodes, args.steps, ms)
-    bytes_step = ALG_BYTES_PER_NODE["f32"] * nodes
+    bytes_step = ALG_BYTES_PER_NODE[args.storage] * nodes
     achieved = bytes_step / (ms_step / 1e3) / 1e9
     out = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{args.n}^3 coupled step: D3Q19 flow + D3Q7 phi/cA/cB, FP32 storage, "
+        "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+        "config": {"workload": f"{args.n}^3 coupled step: D3Q19 flow + D3Q7 phi/cA/cB, {args.storage.upper()} storage, "
                                "walls at z ends, droplets 0.2 vol. frac., r in [6,16], seed 3",
-                   "lattice": [p.nx, p.ny, p.nz], "storage": "f32",
+                   "lattice": [p.nx, p.ny, p.nz], "storage": args.storage,
                    "l2": "state 21.5 GB >> 129 MB L2, no flush", "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "traffic": None if NCU_DRAM_BYTES_PER_NODE_F32 is None else NCU_DRAM_BYTES_PER_NODE_F32 * nodes,
-                     "kernel": "fused_flow_kernel<float> (z-marching fused phi + collide + stream)",
+                     "traffic": (None if NCU_DRAM_BYTES_PER_NODE_F32 is None or args.storage != "f32"
+                                 else NCU_DRAM_BYTES_PER_NODE_F32 * nodes),
+                     "kernel": f"fused_flow_kernel<{'float' if args.storage == 'f32' else args.storage}> "
+                               "(z-marching fused phi + collide + stream)",
                      "alg_bytes_per_launch": bytes_step, "ms_per_launch": ms_step,
                      "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
                      "whole_step_frac": bytes_step / (ms / args.steps / 1e3) / 1e9 / peak,

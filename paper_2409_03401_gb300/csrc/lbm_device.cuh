@@ -171,33 +171,38 @@ template <class T> __device__ inline T from_f(float v);
 template <> __device__ inline __half from_f<__half>(float v) { return __float2half_rn(v); }
 template <> __device__ inline __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
 
+// 16-bit storage holds each moving population P_k as its scaled deviation q_k:
+//   f: P = (w / kFScale) q,  g: P = w (q + 1/2),  h: P = (w / kHScale) q,
+// so that q is O(1) for every set. Kernels load q as it is (a Node of a 16-bit state holds
+// q_k for k > 0 and the FP32 rest population for k = 0), run the collision on q (the
+// BGK update is affine, so it keeps its form with the weights divided out) and store q.
 template <class H> struct Codec16 {
-    // q = P / w - ref, scaled: f (ref 0, x f_scale), g (ref 1/2), h (ref 0, x 64)
-    template <int SET>
-    __device__ static float load(const H* p, double w, const DevParams& P) {
-        const float q = to_f(*p);
-        if (SET == SET_F) return q * float(w / kFScale);
-        if (SET == SET_G) return float(w) * (q + 0.5f);
-        return q * float(w / kHScale);
+    // population = scale * q + offset
+    template <int SET> __host__ __device__ static constexpr double scale(double w) {
+        return SET == SET_F ? w / kFScale : (SET == SET_G ? w : w / kHScale);
+    }
+    template <int SET> __host__ __device__ static constexpr double offset(double w) {
+        return SET == SET_G ? 0.5 * w : 0.0;
     }
     template <int SET>
-    __device__ static H encode(float v, double w, const DevParams& P) {
+    __device__ static float load(const H* p, double, const DevParams&) { return to_f(*p); }
+    // encode a population given in natural units (initial state)
+    template <int SET>
+    __device__ static void store(H* p, float v, double w, const DevParams&) {
         float q;
         if (SET == SET_F) q = v * float(kFScale / w);
         else if (SET == SET_G) q = v * float(1.0 / w) - 0.5f;
         else q = v * float(kHScale / w);
-        return from_f<H>(q);
+        *p = from_f<H>(q);
     }
-    template <int SET>
-    __device__ static void store(H* p, float v, double w, const DevParams& P) { *p = encode<SET>(v, w, P); }
-    // Store and return the rounding residual v - decode(encode(v)). The caller adds the
-    // residuals of a node's moving populations to its FP32 rest population, so the node's
-    // sum over k (phi, c, p_h) is kept to FP32 accuracy and rounding cannot act as a source.
-    template <int SET>
-    __device__ static float store_residual(H* p, float v, double w, const DevParams& P) {
-        const H h = encode<SET>(v, w, P);
+    // Store q and return what rounding removed, q - round16(q) (exact in FP32). The caller
+    // adds scale * residual of a node's moving populations to its FP32 rest population, so
+    // the node's sum over k (phi, c, p_h) keeps FP32 accuracy and rounding cannot act as a
+    // source.
+    __device__ static float store_q(H* p, float q) {
+        const H h = from_f<H>(q);
         *p = h;
-        return v - load<SET>(&h, w, P);
+        return q - to_f(h);
     }
 };
 template <> struct Codec<__half> : Codec16<__half> {};
@@ -255,11 +260,6 @@ __device__ __forceinline__ void store_scalar(const StateView& st, int k, Slot s,
     if (is16<T>() && k == 0) { st.rest[RP * P.plane + s.node] = float(v); return; }
     Codec<T>::template store<SET>(element<T, B>(st, k, s), v, Scalar<LAT>::w(k), P);
 }
-// moving population k > 0; returns the rounding residual of 16-bit storage (0 otherwise)
-template <class T, int SET, int LAT, int B>
-__device__ __forceinline__ typename RealOf<T>::type store_moving(const StateView& st, int k, Slot s,
-                                                                 typename RealOf<T>::type v, const DevParams& P) {
-    return Codec<T>::template store_residual<SET>(element<T, B>(st, k, s), v, Scalar<LAT>::w(k), P);
-}
+
 
 }  // namespace lbm

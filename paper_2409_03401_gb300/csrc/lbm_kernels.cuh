@@ -140,13 +140,56 @@ struct Node {
         gather_flow(st, ad, P);
     }
 
-    // Eq. 49 without the source, Eq. 52 (as c - c_0^eq), Eq. 33 at phi~ and Eq. 35
+    // Eq. 49 without the source, Eq. 52 (as c - c_0^eq), Eq. 33 at phi~ and Eq. 35. With
+    // 16-bit storage the moving populations are scaled deviations q_k (Codec16): the sums
+    // weight them back, sum_k P_k = P_0 + sum_k>0 (scale_k q_k + offset_k).
     __device__ __forceinline__ void moments(const DevParams& P) {
-        phit = R(0); dcA = R(0); dcB = R(0);
+        if constexpr (is16<T>()) {
+            using C = Codec<T>;
+            phit = g[0] + R(0.5 * (1.0 - Scalar<LAT>::w(0)));      // sum of the offsets w_k / 2
+            dcA = hA[0];
+            dcB = hB[0];
 #pragma unroll
-        for (int k = 0; k < Q; ++k) { phit += g[k]; dcA += hA[k]; dcB += hB[k]; }
+            for (int k = 1; k < Q; ++k) {
+                phit += R(C::template scale<SET_G>(Scalar<LAT>::w(k))) * g[k];
+                dcA += R(C::template scale<SET_H>(Scalar<LAT>::w(k))) * hA[k];
+                dcB += R(C::template scale<SET_H>(Scalar<LAT>::w(k))) * hB[k];
+            }
+        } else {
+            phit = R(0); dcA = R(0); dcB = R(0);
+#pragma unroll
+            for (int k = 0; k < Q; ++k) { phit += g[k]; dcA += hA[k]; dcB += hB[k]; }
+        }
         const R pt = interp_p(phit);
         S = source(phit, closure_dev(dcA, pt, 0, P), closure_dev(dcB, pt, 1, P), P);
+    }
+    // p_h = sum f (Eq. 40)
+    __device__ __forceinline__ R flow_p() const {
+        static_assert(FLOW, "flow moments of a node without flow populations");
+        if constexpr (is16<T>()) {
+            R ph = f[0];
+#pragma unroll
+            for (int k = 1; k < 19; ++k) ph += R(Codec<T>::template scale<SET_F>(D3Q19::w(k))) * f[k];
+            return ph;
+        } else {
+            R ph = R(0);
+#pragma unroll
+            for (int k = 0; k < 19; ++k) ph += f[k];
+            return ph;
+        }
+    }
+    // j = sum f e (Eq. 41 before the force shift)
+    __device__ __forceinline__ void flow_j(R& jx, R& jy, R& jz) const {
+        static_assert(FLOW, "flow moments of a node without flow populations");
+        jx = jy = jz = R(0);
+#pragma unroll
+        for (int k = 1; k < 19; ++k) {
+            R v = f[k];
+            if constexpr (is16<T>()) v *= R(Codec<T>::template scale<SET_F>(D3Q19::w(k)));
+            if (D3Q19::ex(k)) jx += R(D3Q19::ex(k)) * v;
+            if (D3Q19::ey(k)) jy += R(D3Q19::ey(k)) * v;
+            if (D3Q19::ez(k)) jz += R(D3Q19::ez(k)) * v;
+        }
     }
     __device__ __forceinline__ R phi() const { return phit + R(0.5) * S; }
     __device__ __forceinline__ R cA(const DevParams& P) const { return dcA + coef<R>(P).c0[0]; }
@@ -172,20 +215,15 @@ __device__ __forceinline__ void stencil(Get get, R phic, R& gx, R& gy, R& gz, R&
 }
 
 // Total force (Eq. 34 + Boussinesq) and velocity (Eq. 41).
-template <class R>
-__device__ __forceinline__ void force_velocity(const R* f, R phi, R gx, R gy, R gz, R lap, const DevParams& P,
+template <class NodeT, class R>
+__device__ __forceinline__ void force_velocity(const NodeT& nd, R phi, R gx, R gy, R gz, R lap, const DevParams& P,
                                                R& Fx, R& Fy, R& Fz, R& ux, R& uy, R& uz) {
     const R br = coef<R>(P).sw15 * (dwell_d(phi) * coef<R>(P).inv_W2 - lap);
     Fx = br * gx + phi * coef<R>(P).g[0];
     Fy = br * gy + phi * coef<R>(P).g[1];
     Fz = br * gz + phi * coef<R>(P).g[2];
-    R jx = R(0), jy = R(0), jz = R(0);
-#pragma unroll
-    for (int k = 1; k < 19; ++k) {
-        if (D3Q19::ex(k)) jx += R(D3Q19::ex(k)) * f[k];
-        if (D3Q19::ey(k)) jy += R(D3Q19::ey(k)) * f[k];
-        if (D3Q19::ez(k)) jz += R(D3Q19::ez(k)) * f[k];
-    }
+    R jx, jy, jz;
+    nd.flow_j(jx, jy, jz);
     ux = R(3) * jx + R(0.5) * Fx;
     uy = R(3) * jy + R(0.5) * Fy;
     uz = R(3) * jz + R(0.5) * Fz;
@@ -212,6 +250,10 @@ __device__ __forceinline__ R edot(int ex, int ey, int ez, R vx, R vy, R vz) {
 //       f^eq = w (B + cu (1 + 1.5 cu)) - F_k / 2, B = p_h - 0.5 u^2          (Eqs. 36-39)
 //   g:  g^eq = w (phi - S/2 + phi cu / cs2), g* = g - om (g - g^eq) + w S    (Eqs. 46-48)
 //   h:  h^eq_k = w (mu + c cu / cs2), h^eq_0 = dc - (1 - w_0) mu (shifted)   (Eqs. 50-51)
+// With 16-bit storage the moving populations are updated as scaled deviations q (Codec16):
+// every term above carries the factor w_k, so dividing it out leaves the same affine update
+// on q with the per-direction weights gone, e.g. q*_f = q - om (q - s E_k) + s G_k with
+// E_k = f^eq / w, G_k = F_k / w, s = kFScale.
 template <class T, int LAT, bool FLOW, class A>
 __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, typename RealOf<T>::type phi,
                                               typename RealOf<T>::type ux, typename RealOf<T>::type uy,
@@ -223,52 +265,88 @@ __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, type
     constexpr int Q = L::Q;
     const int self = ad.self;
     if constexpr (FLOW) {
-        R ph = R(0);
-#pragma unroll
-        for (int k = 0; k < 19; ++k) ph += nd.f[k];
+        const R ph = nd.flow_p();
         const R usq = ux * ux + uy * uy + uz * uz;
         const R Ac = R(1) - R(1.5) * usq;
         const R Bc = ph - R(0.5) * usq;
         const R uF = ux * Fx + uy * Fy + uz * Fz;
         const R omf = coef<R>(P).om_f;
-        R f0post = R(0), resid = R(0);
-        // forcing term F_k (Eqs. 37-38) and shifted equilibrium (Eq. 39) of direction k
-        auto force_eq = [&](int k, R& Fk, R& feq) {
+        // G = F_k / w_k (Eqs. 37-38) and E = f^eq_k / w_k (Eq. 39) of direction k
+        auto force_eq = [&](int k, R& G, R& E) {
             const int ex = D3Q19::ex(k), ey = D3Q19::ey(k), ez = D3Q19::ez(k);
-            const R w = R(D3Q19::w(k));
             const R cu = edot(ex, ey, ez, ux, uy, uz);
-            Fk = w * (Ac + cu * (R(3) + R(4.5) * cu)) * (edot(ex, ey, ez, Fx, Fy, Fz) - uF);
-            feq = w * (Bc + cu * (R(1) + R(1.5) * cu)) - R(0.5) * Fk;
+            G = (Ac + cu * (R(3) + R(4.5) * cu)) * (edot(ex, ey, ez, Fx, Fy, Fz) - uF);
+            E = Bc + cu * (R(1) + R(1.5) * cu) - R(0.5) * G;
         };
-        auto put = [&](int k, R post) {
-            if (is16<T>() && k == 0) { f0post = post; return; }
-            const Slot s = ad.dst(k, D3Q19::ex(k), D3Q19::ey(k), D3Q19::ez(k));
-            resid += Codec<T>::template store_residual<SET_F>(element<T, 0>(out, k, s), post, D3Q19::w(k), P);
-        };
-        if (!P.trt) {                                     // BGK, Eq. 36
+        if constexpr (!is16<T>()) {
+            auto put = [&](int k, R post) {
+                const Slot s = ad.dst(k, D3Q19::ex(k), D3Q19::ey(k), D3Q19::ez(k));
+                *element<T, 0>(out, k, s) = post;
+            };
+            // F_k and f^eq_k in natural units
+            auto force_eq_w = [&](int k, R& Fk, R& feq) {
+                const int ex = D3Q19::ex(k), ey = D3Q19::ey(k), ez = D3Q19::ez(k);
+                const R w = R(D3Q19::w(k));
+                const R cu = edot(ex, ey, ez, ux, uy, uz);
+                Fk = w * (Ac + cu * (R(3) + R(4.5) * cu)) * (edot(ex, ey, ez, Fx, Fy, Fz) - uF);
+                feq = w * (Bc + cu * (R(1) + R(1.5) * cu)) - R(0.5) * Fk;
+            };
+            if (!P.trt) {                                     // BGK, Eq. 36
 #pragma unroll
-            for (int k = 0; k < 19; ++k) {
-                R Fk, feq;
-                force_eq(k, Fk, feq);
-                put(k, nd.f[k] - omf * (nd.f[k] - feq) + Fk);
-            }
-        } else {                                          // two relaxation times
-            const R omm = coef<R>(P).om_fm;
-            R F0, feq0;
-            force_eq(0, F0, feq0);
-            put(0, nd.f[0] - omf * (nd.f[0] - feq0) + F0);
+                for (int k = 0; k < 19; ++k) {
+                    R Fk, feq;
+                    force_eq_w(k, Fk, feq);
+                    put(k, nd.f[k] - omf * (nd.f[k] - feq) + Fk);
+                }
+            } else {                                          // two relaxation times
+                const R omm = coef<R>(P).om_fm;
+                R F0, feq0;
+                force_eq_w(0, F0, feq0);
+                put(0, nd.f[0] - omf * (nd.f[0] - feq0) + F0);
 #pragma unroll
-            for (int k = 1; k < 19; k += 2) {             // pairs (k, opp(k) = k + 1)
-                R Fa, ea, Fb, eb;
-                force_eq(k, Fa, ea);
-                force_eq(k + 1, Fb, eb);
-                const R da = nd.f[k] - ea, db = nd.f[k + 1] - eb;
-                const R even = R(0.5) * (da + db), odd = R(0.5) * (da - db);
-                put(k, nd.f[k] - omf * even - omm * odd + Fa);
-                put(k + 1, nd.f[k + 1] - omf * even + omm * odd + Fb);
+                for (int k = 1; k < 19; k += 2) {             // pairs (k, opp(k) = k + 1)
+                    R Fa, ea, Fb, eb;
+                    force_eq_w(k, Fa, ea);
+                    force_eq_w(k + 1, Fb, eb);
+                    const R da = nd.f[k] - ea, db = nd.f[k + 1] - eb;
+                    const R even = R(0.5) * (da + db), odd = R(0.5) * (da - db);
+                    put(k, nd.f[k] - omf * even - omm * odd + Fa);
+                    put(k + 1, nd.f[k + 1] - omf * even + omm * odd + Fb);
+                }
             }
+        } else {
+            constexpr float s = kFScale;
+            R resid = R(0);                                   // in natural units
+            auto put = [&](int k, R q) {
+                const Slot sl = ad.dst(k, D3Q19::ex(k), D3Q19::ey(k), D3Q19::ez(k));
+                resid += R(Codec<T>::template scale<SET_F>(D3Q19::w(k))) * Codec<T>::store_q(element<T, 0>(out, k, sl), q);
+            };
+            R G0, E0;                                         // rest population in natural units
+            force_eq(0, G0, E0);
+            const R w0 = R(D3Q19::w(0));
+            const R f0post = nd.f[0] - omf * (nd.f[0] - w0 * E0) + w0 * G0;
+            if (!P.trt) {
+#pragma unroll
+                for (int k = 1; k < 19; ++k) {
+                    R G, E;
+                    force_eq(k, G, E);
+                    put(k, nd.f[k] - omf * (nd.f[k] - s * E) + s * G);
+                }
+            } else {
+                const R omm = coef<R>(P).om_fm;
+#pragma unroll
+                for (int k = 1; k < 19; k += 2) {
+                    R Ga, Ea, Gb, Eb;
+                    force_eq(k, Ga, Ea);
+                    force_eq(k + 1, Gb, Eb);
+                    const R da = nd.f[k] - s * Ea, db = nd.f[k + 1] - s * Eb;
+                    const R even = R(0.5) * (da + db), odd = R(0.5) * (da - db);
+                    put(k, nd.f[k] - omf * even - omm * odd + s * Ga);
+                    put(k + 1, nd.f[k + 1] - omf * even + omm * odd + s * Gb);
+                }
+            }
+            out.rest[3 * P.plane + self] = float(f0post + resid);
         }
-        if (is16<T>()) out.rest[3 * P.plane + self] = float(f0post + resid);
     }
     const R p = interp_p(phi);
     const R muA = closure_dev(nd.dcA, p, 0, P);
@@ -282,27 +360,50 @@ __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, type
     const R ga = phi - R(0.5) * nd.S;                                 // g^eq = w (ga + gb cu)
     const R gb = phi * inv_cs2;
     const R cAu = nd.cA(P) * inv_cs2, cBu = nd.cB(P) * inv_cs2;
-    R g0 = R(0), hA0 = R(0), hB0 = R(0);                              // rest populations, stored last
+    // rest populations (natural units in every storage), stored last
+    const R w0 = R(L::w(0));
+    R g0, hA0, hB0;
+    if constexpr (!is16<T>()) {
 #pragma unroll
-    for (int k = 0; k < Q; ++k) {
-        const int ex = L::ex(k), ey = L::ey(k), ez = L::ez(k);
-        const R w = R(L::w(k));
-        const R cu = edot(ex, ey, ez, ux, uy, uz);
-        const R geq = w * (ga + gb * cu);
-        const R gpost = nd.g[k] - omg * (nd.g[k] - geq) + w * nd.S;
-        if (k == 0) {                                                 // h_0 shifted by c_0^eq
-            g0 = gpost;
-            hA0 = nd.hA[0] - omA * (nd.hA[0] - (nd.dcA - (R(1) - w) * muA));
-            hB0 = nd.hB[0] - omB * (nd.hB[0] - (nd.dcB - (R(1) - w) * muB));
-            continue;
+        for (int k = 0; k < Q; ++k) {
+            const int ex = L::ex(k), ey = L::ey(k), ez = L::ez(k);
+            const R w = R(L::w(k));
+            const R cu = edot(ex, ey, ez, ux, uy, uz);
+            const R geq = w * (ga + gb * cu);
+            const R gpost = nd.g[k] - omg * (nd.g[k] - geq) + w * nd.S;
+            if (k == 0) {                                             // h_0 shifted by c_0^eq
+                g0 = gpost;
+                hA0 = nd.hA[0] - omA * (nd.hA[0] - (nd.dcA - (R(1) - w) * muA));
+                hB0 = nd.hB[0] - omB * (nd.hB[0] - (nd.dcB - (R(1) - w) * muB));
+                continue;
+            }
+            const Slot s = ad.dst(k, ex, ey, ez);
+            *element<T, Planes<LAT>::G>(out, k, s) = gpost;
+            *element<T, Planes<LAT>::HA>(out, k, s) = nd.hA[k] - omA * (nd.hA[k] - w * (muA + cAu * cu));
+            *element<T, Planes<LAT>::HB>(out, k, s) = nd.hB[k] - omB * (nd.hB[k] - w * (muB + cBu * cu));
         }
-        const R hApost = nd.hA[k] - omA * (nd.hA[k] - w * (muA + cAu * cu));
-        const R hBpost = nd.hB[k] - omB * (nd.hB[k] - w * (muB + cBu * cu));
-        const Slot s = ad.dst(k, ex, ey, ez);
-        // 16-bit storage: rounding residuals of the moving populations go to the rest population
-        g0 += store_moving<T, SET_G, LAT, Planes<LAT>::G>(out, k, s, gpost, P);
-        hA0 += store_moving<T, SET_H, LAT, Planes<LAT>::HA>(out, k, s, hApost, P);
-        hB0 += store_moving<T, SET_H, LAT, Planes<LAT>::HB>(out, k, s, hBpost, P);
+    } else {
+        g0 = nd.g[0] - omg * (nd.g[0] - w0 * ga) + w0 * nd.S;
+        hA0 = nd.hA[0] - omA * (nd.hA[0] - (nd.dcA - (R(1) - w0) * muA));   // h_0 shifted by c_0^eq
+        hB0 = nd.hB[0] - omB * (nd.hB[0] - (nd.dcB - (R(1) - w0) * muB));
+        // q-space: g = w (q + 1/2) gives q* = q - om (q + 1/2 - ga - gb cu) + S, and
+        // h = (w / kHScale) q gives q* = q - om (q - kHScale (mu + c cu / cs2))
+        using C = Codec<T>;
+        const R gq = R(0.5) - ga;
+        const R mA = R(kHScale) * muA, mB = R(kHScale) * muB;
+        const R cA = R(kHScale) * cAu, cB = R(kHScale) * cBu;
+#pragma unroll
+        for (int k = 1; k < Q; ++k) {
+            const int ex = L::ex(k), ey = L::ey(k), ez = L::ez(k);
+            const R cu = edot(ex, ey, ez, ux, uy, uz);
+            const Slot s = ad.dst(k, ex, ey, ez);
+            const R qg = nd.g[k] - omg * (nd.g[k] + gq - gb * cu) + nd.S;
+            const R qA = nd.hA[k] - omA * (nd.hA[k] - (mA + cA * cu));
+            const R qB = nd.hB[k] - omB * (nd.hB[k] - (mB + cB * cu));
+            g0 += R(C::template scale<SET_G>(L::w(k))) * C::store_q(element<T, Planes<LAT>::G>(out, k, s), qg);
+            hA0 += R(C::template scale<SET_H>(L::w(k))) * C::store_q(element<T, Planes<LAT>::HA>(out, k, s), qA);
+            hB0 += R(C::template scale<SET_H>(L::w(k))) * C::store_q(element<T, Planes<LAT>::HB>(out, k, s), qB);
+        }
     }
     const Slot s0{self, 0};
     store_scalar<T, SET_G, LAT, Planes<LAT>::G, 0>(out, 0, s0, g0, P);
@@ -333,7 +434,7 @@ step_kernel(const DevParams P, const StateView st, const StateView out,
     if constexpr (FLOW) {
         R gx, gy, gz, lap;
         stencil([&](int dx, int dy, int dz) { return ad.phi(phi_field, dx, dy, dz); }, phi, gx, gy, gz, lap);
-        force_velocity(nd.f, phi, gx, gy, gz, lap, P, Fx, Fy, Fz, ux, uy, uz);
+        force_velocity(nd, phi, gx, gy, gz, lap, P, Fx, Fy, Fz, ux, uy, uz);
     }
     collide_store(nd, phi, ux, uy, uz, Fx, Fy, Fz, out, ad, P);
 }
@@ -506,7 +607,7 @@ fused_flow_kernel(const DevParams P, const StateView src, const StateView dst, i
                     const int s = dz < 0 ? sp : (dz > 0 ? sn : sc);
                     return ring[s][ty + 1 + dy][tx + 1 + dx];
                 }, phi, gx, gy, gz, lap);
-        force_velocity(nd.f, phi, gx, gy, gz, lap, P, Fx, Fy, Fz, ux, uy, uz);
+        force_velocity(nd, phi, gx, gy, gz, lap, P, Fx, Fy, Fz, ux, uy, uz);
         collide_store(nd, phi, ux, uy, uz, Fx, Fy, Fz, dst, ad, P);
     };
 
@@ -605,11 +706,8 @@ fields_kernel(const DevParams P, const StateView st, const typename RealOf<T>::t
     if constexpr (FLOW) {
         R gx, gy, gz, lap, Fx, Fy, Fz;
         stencil([&](int dx, int dy, int dz) { return ad.phi(phi_field, dx, dy, dz); }, phi, gx, gy, gz, lap);
-        force_velocity(nd.f, phi, gx, gy, gz, lap, P, Fx, Fy, Fz, vals[6], vals[7], vals[8]);
-        R ph = R(0);
-#pragma unroll
-        for (int k = 0; k < 19; ++k) ph += nd.f[k];
-        vals[5] = ph;
+        force_velocity(nd, phi, gx, gy, gz, lap, P, Fx, Fy, Fz, vals[6], vals[7], vals[8]);
+        vals[5] = nd.flow_p();
     }
 #pragma unroll
     for (int i = 0; i < LBM_NFIELDS_DEV; ++i)
@@ -667,12 +765,9 @@ reduce_kernel(const DevParams P, const StateView st, const typename RealOf<T>::t
         if constexpr (FLOW) {
             R gx, gy, gz, lap, Fx, Fy, Fz, ux, uy, uz;
             stencil([&](int dx, int dy, int dz) { return ad.phi(phi_field, dx, dy, dz); }, phi, gx, gy, gz, lap);
-            force_velocity(nd.f, phi, gx, gy, gz, lap, P, Fx, Fy, Fz, ux, uy, uz);
+            force_velocity(nd, phi, gx, gy, gz, lap, P, Fx, Fy, Fz, ux, uy, uz);
             umag = sqrt(double(ux) * ux + double(uy) * uy + double(uz) * uz);
-            R s = R(0);
-#pragma unroll
-            for (int k = 0; k < 19; ++k) s += nd.f[k];
-            ph = s;
+            ph = nd.flow_p();
         }
         const double vals[5] = {double(phi), double(nd.dcA) + P.c0[0], double(nd.dcB) + P.c0[1], ph,
                                 double(nd.S)};
