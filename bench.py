@@ -251,6 +251,15 @@ def run_e2e(p, init, steps, device):
             "steps": steps, "seconds": dt}
 
 
+def config_of(args, p, ws):
+    """The workload both arms report (the reference arm times bounded samples of it)."""
+    label = {"f32": "FP32", "f16": "FP16", "bf16": "BF16"}[args.storage]
+    return {"workload": f"{args.n}^3 coupled step: D3Q19 flow + D3Q7 phi/cA/cB, {label} storage, "
+                        "walls at z ends, droplets 0.2 vol. frac., r in [6,16], seed 3",
+            "lattice": [p.nx, p.ny, p.nz], "storage": args.storage,
+            "l2": "state 21.5 GB >> 129 MB L2, no flush", "parallelism": f"replicas x{ws}"}
+
+
 def gb300(args):
     import torch
     ws, rank, local = dist_env()
@@ -282,10 +291,7 @@ def gb300(args):
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
-        "config": {"workload": f"{args.n}^3 coupled step: D3Q19 flow + D3Q7 phi/cA/cB, {args.storage.upper()} storage, "
-                               "walls at z ends, droplets 0.2 vol. frac., r in [6,16], seed 3",
-                   "lattice": [p.nx, p.ny, p.nz], "storage": args.storage,
-                   "l2": "state 21.5 GB >> 129 MB L2, no flush", "parallelism": f"replicas x{ws}"},
+        "config": config_of(args, p, ws),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      "traffic": (None if NCU_DRAM_BYTES_PER_NODE_F32 is None or args.storage != "f32"
@@ -374,6 +380,9 @@ def gb300(args):
 
 
 def reference(args):
+    """The FP64 CPU oracle, as it stands, on the host cores: every step is one oracle step over
+    a z-slab of the same 512^3 workload, the slab sized (2 to 16 planes) so that W + K steps
+    take about a minute."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
@@ -381,27 +390,31 @@ def reference(args):
     from workloads import configs
     from oracle.lbm import OracleLBM
     p, fields_fn = configs.sedimentation(n=args.n)
-    # each reference "step" is one oracle step over a bounded slab of the same workload
-    planes = args.cpu_sample_planes
-    z0 = p.nz // 2 - planes // 2
-    q = p.with_(nz=planes)
-    o = OracleLBM(q)
-    o.init(*fields_fn(device="cpu", z_range=(z0, z0 + planes)))
-    steps = min(args.steps, 10)
-    o.step(min(args.warmup, 2))
+
+    def slab(planes):
+        z0 = p.nz // 2 - planes // 2
+        q = p.with_(nz=planes)
+        o = OracleLBM(q)
+        o.init(*fields_fn(device="cpu", z_range=(z0, z0 + planes)))
+        return q, o, z0
+    q, o, _ = slab(2)                                  # calibration: rate of one step
     t0 = time.perf_counter()
-    o.step(steps)
+    o.step(1)
+    rate = q.nodes / (time.perf_counter() - t0)
+    budget = 60.0
+    planes = int(max(2, min(16, budget * rate / ((args.steps + args.warmup) * p.nx * p.ny))))
+    q, o, z0 = slab(planes)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
     dt = time.perf_counter() - t0
-    value = q.nodes * steps / dt / 1e6
+    value = q.nodes * args.steps / dt / 1e6
     sample = (f"{q.nx}x{q.ny}x{planes} slab (z {z0}..{z0 + planes - 1}) of the {args.n}^3 initial fields, "
-              f"walls at the slab ends; {steps} timed steps (of {args.steps} asked) after "
-              f"{min(args.warmup, 2)} untimed")
+              f"walls at the slab ends; {args.steps} timed steps after {args.warmup} untimed")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws,
-           "steps": steps, "warmup": min(args.warmup, 2), "ms_per_step": dt / steps * 1e3,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic",
-           "config": {"workload": f"{args.n}^3 coupled step (bounded slab sample), FP64 CPU oracle",
-                      "lattice": [q.nx, q.ny, q.nz]},
+           "data": "synthetic", "config": config_of(args, p, ws),
            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": torch.get_num_threads(),
                             "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
