@@ -78,3 +78,17 @@ def test_euler_is_zero_on_3d_lattices():
     sim, _ = run_gpu(p, fields(), 2)
     s = sim.sums()
     assert s["euler"] == 0.0 and s["interface"] > 0
+
+
+def test_full_size_4096_squared_matches_oracle():
+    # the 4096^2 D2Q9 run as the bench times it (FP32, in place), against the oracle on the
+    # whole lattice after 3 steps, and the droplet count of the initial field
+    p, fields = configs.ripening_2d()
+    f = fields()
+    sim, g = run_gpu(p, [t.cuda() for t in f], 3)
+    _, r = run_oracle(p, f, 3)
+    from parity import rel_linf
+    errs = {k: rel_linf(g[k], r[k], k) for k in ("phi", "muA", "muB", "cA", "cB")}
+    _close(errs, TOL["f32"])
+    s = sim.sums()
+    assert s["euler"] == float(measure.count_droplets(g["phi"].cpu().numpy()))
