@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--cpu-sample-steps", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle leg (profiling runs)")
     ap.add_argument("--adjoint-only", action="store_true", help="time only the adjoint variant (profiling runs)")
+    ap.add_argument("--drift", type=int, default=0, metavar="STEPS",
+                    help="instead of the bench: the 384^3 drift study of sum phi and sum c (FP32 vs 16-bit)")
+    ap.add_argument("--ripening-law", type=int, default=0, metavar="STEPS",
+                    help="instead of the bench: <R>^3 against t on the 256^3 (3D) and 4096^2 (2D) ripening runs")
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                     help="population storage of the main line (profiling runs; the headline is f32)")
     ap.add_argument("--adjoint-steps", type=int, default=200)
@@ -421,9 +425,92 @@ def reference(args):
     print(json.dumps(out))
 
 
+def drift_study(args):
+    """Drift of the invariants sum c^A, sum c^B and of sum phi over a long run of the
+    384^3 wall-bounded flow workload (droplets at 0.1, r in [8, 20]), FP32 against FP16 and
+    BF16 storage; the FP64 sums come from the library's reduction."""
+    import torch
+    from workloads import configs
+    from paper_2409_03401_gb300 import Simulation
+    torch.cuda.set_device(0)
+    p, fields = configs.drift()
+    init = fields(device="cuda")
+    every = max(1, args.drift // 10)
+    runs = {}
+    for storage in ("f32", "f16", "bf16"):
+        sim = Simulation(p.with_(storage=storage), *init, device="cuda")
+        series = []
+        t0 = time.perf_counter()
+        for t in range(0, args.drift + 1, every):
+            if t:
+                sim.step(every)
+            s = sim.sums()
+            series.append({"t": t, "phi": s["phi"], "cA": s["cA"], "cB": s["cB"], "p": s["p"], "umax": s["umax"]})
+        torch.cuda.synchronize()
+        runs[storage] = {"series": series, "seconds": time.perf_counter() - t0}
+        del sim
+        torch.cuda.empty_cache()
+    ref = runs["f32"]["series"]
+    out = {"study": "drift", "workload": "384^3, walls at z ends, D3Q19 flow + D3Q7, droplets 0.1, r in [8,20], seed 4",
+           "steps": args.drift, "sample_every": every, "runs": {}}
+    for storage, r in runs.items():
+        s0, s1 = r["series"][0], r["series"][-1]
+        out["runs"][storage] = {
+            "rel_drift_cA": (s1["cA"] - s0["cA"]) / s0["cA"], "rel_drift_cB": (s1["cB"] - s0["cB"]) / s0["cB"],
+            "max_rel_dev_phi_vs_f32": max(abs(a["phi"] - b["phi"]) / abs(b["phi"]) for a, b in zip(r["series"], ref)),
+            "phi_change": (s1["phi"] - s0["phi"]) / s0["phi"], "umax_end": s1["umax"], "seconds": r["seconds"],
+            "series": r["series"]}
+    print(json.dumps(out))
+
+
+def ripening_law(args):
+    """<R>^3 against t. 3D (256^3, D3Q7, FP32): the Sauter radius R = 3 V / A from the
+    volume V = sum phi and the interface area A = sum (4/W) phi (1 - phi); 2D (4096^2, D2Q9):
+    <R> = A / (2 pi N) of Eq. 67 with the droplet count N of the Euler characteristic. Least-
+    squares line of <R>^3 over the second half of the run, with its R^2."""
+    import torch
+    from workloads import configs
+    from paper_2409_03401_gb300 import Simulation
+    torch.cuda.set_device(0)
+    out = {"study": "ripening_law", "steps": args.ripening_law, "runs": {}}
+    for name, build in (("3d_256", lambda: configs.ripening()), ("2d_4096", lambda: configs.ripening_2d())):
+        p, fields = build()
+        sim = Simulation(p, *fields(device="cuda"), device="cuda")
+        every = max(1, args.ripening_law // 20)
+        series = []
+        for t in range(0, args.ripening_law + 1, every):
+            if t:
+                sim.step(every)
+            s = sim.sums()
+            if p.nz == 1:
+                R = s["interface"] / (2 * math.pi * s["euler"]) if s["euler"] > 0 else float("nan")
+                series.append({"t": t, "R": R, "N": s["euler"]})
+            else:
+                series.append({"t": t, "R": 3.0 * s["phi"] / s["interface"]})
+        half = [e for e in series if e["t"] >= args.ripening_law / 2]
+        ts = [e["t"] for e in half]
+        ys = [e["R"] ** 3 for e in half]
+        n = len(ts)
+        mt, my = sum(ts) / n, sum(ys) / n
+        sxx = sum((a - mt) ** 2 for a in ts)
+        sxy = sum((a - mt) * (b - my) for a, b in zip(ts, ys))
+        slope = sxy / sxx
+        ss_res = sum((b - (my + slope * (a - mt))) ** 2 for a, b in zip(ts, ys))
+        ss_tot = sum((b - my) ** 2 for b in ys)
+        out["runs"][name] = {"R3_slope_per_step": slope, "R3_fit_r2": 1.0 - ss_res / ss_tot if ss_tot > 0 else None,
+                             "series": series}
+        del sim
+        torch.cuda.empty_cache()
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.drift:
+        drift_study(args)
+    elif args.ripening_law:
+        ripening_law(args)
+    elif args.impl == "reference":
         reference(args)
     else:
         gb300(args)
