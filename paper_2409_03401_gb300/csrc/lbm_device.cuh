@@ -195,14 +195,17 @@ template <class H> struct Codec16 {
         else q = v * float(kHScale / w);
         *p = from_f<H>(q);
     }
-    // Store q and return what rounding removed, q - round16(q) (exact in FP32). The caller
-    // adds scale * residual of a node's moving populations to its FP32 rest population, so
-    // the node's sum over k (phi, c, p_h) keeps FP32 accuracy and rounding cannot act as a
-    // source.
+    // Store q and return what rounding removed, q - round16(q) (exact in FP32).
     __device__ static float store_q(H* p, float q) {
         const H h = from_f<H>(q);
         *p = h;
         return q - to_f(h);
+    }
+    // Store q and return the stored value read back, round16(q).
+    __device__ static float store_q_back(H* p, float q) {
+        const H h = from_f<H>(q);
+        *p = h;
+        return to_f(h);
     }
 };
 template <> struct Codec<__half> : Codec16<__half> {};

@@ -316,15 +316,12 @@ __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, type
             }
         } else {
             constexpr float s = kFScale;
-            R resid = R(0);                                   // in natural units
+            R stored = R(0);                                  // sum of the stored moving f, natural units
             auto put = [&](int k, R q) {
                 const Slot sl = ad.dst(k, D3Q19::ex(k), D3Q19::ey(k), D3Q19::ez(k));
-                resid += R(Codec<T>::template scale<SET_F>(D3Q19::w(k))) * Codec<T>::store_q(element<T, 0>(out, k, sl), q);
+                stored += R(Codec<T>::template scale<SET_F>(D3Q19::w(k))) *
+                          Codec<T>::store_q_back(element<T, 0>(out, k, sl), q);
             };
-            R G0, E0;                                         // rest population in natural units
-            force_eq(0, G0, E0);
-            const R w0 = R(D3Q19::w(0));
-            const R f0post = nd.f[0] - omf * (nd.f[0] - w0 * E0) + w0 * G0;
             if (!P.trt) {
 #pragma unroll
                 for (int k = 1; k < 19; ++k) {
@@ -345,7 +342,10 @@ __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, type
                     put(k + 1, nd.f[k + 1] - omf * even + omm * odd + s * Gb);
                 }
             }
-            out.rest[3 * P.plane + self] = float(f0post + resid);
+            // the collision keeps sum_k f_k = p_h (BGK and TRT alike: sum f^eq = p_h, sum F_k = 0),
+            // so the FP32 rest population takes p_h minus what the moving ones stored: the
+            // node's p_h survives the 16-bit rounding
+            out.rest[3 * P.plane + self] = float(ph - stored);
         }
     }
     const R p = interp_p(phi);
@@ -361,7 +361,6 @@ __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, type
     const R gb = phi * inv_cs2;
     const R cAu = nd.cA(P) * inv_cs2, cBu = nd.cB(P) * inv_cs2;
     // rest populations (natural units in every storage), stored last
-    const R w0 = R(L::w(0));
     R g0, hA0, hB0;
     if constexpr (!is16<T>()) {
 #pragma unroll
@@ -383,9 +382,11 @@ __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, type
             *element<T, Planes<LAT>::HB>(out, k, s) = nd.hB[k] - omB * (nd.hB[k] - w * (muB + cBu * cu));
         }
     } else {
-        g0 = nd.g[0] - omg * (nd.g[0] - w0 * ga) + w0 * nd.S;
-        hA0 = nd.hA[0] - omA * (nd.hA[0] - (nd.dcA - (R(1) - w0) * muA));   // h_0 shifted by c_0^eq
-        hB0 = nd.hB[0] - omB * (nd.hB[0] - (nd.dcB - (R(1) - w0) * muB));
+        // the collisions keep sum g = phi~ + S and sum h = c - c_0^eq (Eqs. 47-48, 51 with the
+        // shifted h_0); each rest population takes that total minus what the moving ones stored
+        g0 = phi + R(0.5) * nd.S - R(0.5 * (1.0 - L::w(0)));       // phi~ + S = phi + S/2
+        hA0 = nd.dcA;
+        hB0 = nd.dcB;
         // q-space: g = w (q + 1/2) gives q* = q - om (q + 1/2 - ga - gb cu) + S, and
         // h = (w / kHScale) q gives q* = q - om (q - kHScale (mu + c cu / cs2))
         using C = Codec<T>;
@@ -400,9 +401,9 @@ __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, type
             const R qg = nd.g[k] - omg * (nd.g[k] + gq - gb * cu) + nd.S;
             const R qA = nd.hA[k] - omA * (nd.hA[k] - (mA + cA * cu));
             const R qB = nd.hB[k] - omB * (nd.hB[k] - (mB + cB * cu));
-            g0 += R(C::template scale<SET_G>(L::w(k))) * C::store_q(element<T, Planes<LAT>::G>(out, k, s), qg);
-            hA0 += R(C::template scale<SET_H>(L::w(k))) * C::store_q(element<T, Planes<LAT>::HA>(out, k, s), qA);
-            hB0 += R(C::template scale<SET_H>(L::w(k))) * C::store_q(element<T, Planes<LAT>::HB>(out, k, s), qB);
+            g0 -= R(C::template scale<SET_G>(L::w(k))) * C::store_q_back(element<T, Planes<LAT>::G>(out, k, s), qg);
+            hA0 -= R(C::template scale<SET_H>(L::w(k))) * C::store_q_back(element<T, Planes<LAT>::HA>(out, k, s), qA);
+            hB0 -= R(C::template scale<SET_H>(L::w(k))) * C::store_q_back(element<T, Planes<LAT>::HB>(out, k, s), qB);
         }
     }
     const Slot s0{self, 0};
