@@ -48,9 +48,10 @@ typedef enum { LBM_D2Q5 = 0, LBM_D3Q7 = 1, LBM_D3Q19 = 2, LBM_D2Q9 = 3 } lbm_lat
 /* Storage type of the populations. Arithmetic is FP64 for LBM_F64 and FP32 otherwise.
  * LBM_F16 / LBM_BF16 store every moving population as a 16-bit deviation from its
  * lattice-weight reference, q_k = P_k / w_k - ref (f: ref 0 times f_scale; g: ref 1/2;
- * h: ref 0 times 64); the rest populations g_0, h^A_0, h^B_0, f_0 stay FP32 and receive the
- * rounding residual of the node's moving populations at every store, so the node's sums
- * (phi, c^A, c^B, p_h) are carried to FP32 accuracy.
+ * h: ref 0 times 64); the rest populations g_0, h^A_0, h^B_0, f_0 stay FP32. Every step sets
+ * each rest population to its set's conserved total at the node (p_h, phi~ + S, c - c_0^eq)
+ * minus the moving populations as stored, so the node's sums (phi, c^A, c^B, p_h) are
+ * carried to FP32 accuracy and 16-bit rounding cannot act as a source.
  * In every storage type the rest populations h^alpha_0 are kept shifted by the constant
  * c_0^{alpha,eq} (h_0 - c_0^eq), so that the sum of the h populations is c - c_0^eq and
  * mu (Eq. 33) does not inherit the rounding of c itself. */

@@ -156,13 +156,6 @@ template <class T> struct Codec {
     __device__ static typename RealOf<T>::type load(const T* p, double, const DevParams&) { return *p; }
     template <int SET>
     __device__ static void store(T* p, typename RealOf<T>::type v, double, const DevParams&) { *p = v; }
-    // store and return what rounding removed (nothing here)
-    template <int SET>
-    __device__ static typename RealOf<T>::type store_residual(T* p, typename RealOf<T>::type v, double w,
-                                                              const DevParams& P) {
-        *p = v;
-        return typename RealOf<T>::type(0);
-    }
 };
 
 __device__ inline float to_f(__half v) { return __half2float(v); }
@@ -195,13 +188,9 @@ template <class H> struct Codec16 {
         else q = v * float(kHScale / w);
         *p = from_f<H>(q);
     }
-    // Store q and return what rounding removed, q - round16(q) (exact in FP32).
-    __device__ static float store_q(H* p, float q) {
-        const H h = from_f<H>(q);
-        *p = h;
-        return q - to_f(h);
-    }
-    // Store q and return the stored value read back, round16(q).
+    // Store q and return the stored value read back, round16(q): the caller subtracts the
+    // moving populations as stored from the node's conserved total to set its FP32 rest
+    // population, so 16-bit rounding never changes the node's sums.
     __device__ static float store_q_back(H* p, float q) {
         const H h = from_f<H>(q);
         *p = h;
