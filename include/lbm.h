@@ -120,8 +120,9 @@ typedef struct lbm_ctx lbm_ctx;
 /* Bytes of the population state for these parameters (256-byte aligned planes). */
 size_t lbm_state_bytes(const lbm_params* p);
 
-/* Bytes of scratch the step needs beside the state: the phi field read by the
- * capillary stencil (flow only) and the block partials of lbm_reduce. */
+/* Bytes of scratch the step needs beside the state: the phi field (read by the capillary
+ * stencil with flow, and by the droplet count of lbm_reduce on the 2D lattices) and the
+ * block partials of lbm_reduce. */
 size_t lbm_work_bytes(const lbm_params* p);
 
 /* Validate p, bind the caller's device buffers and CUDA stream (cudaStream_t passed as
@@ -229,10 +230,11 @@ lbm_status lbm_adjoint_theta(const lbm_params* p, void* d_adj_work, double* out,
  * application that hands this library its state buffer but owns every allocation, or a
  * real-time loop where allocation is forbidden after start-up). Same results as
  * lbm_reduce for the state copy d_state holds at time t (the buffer lbm_init was given),
- * but the reduction's scratch (block partials, results, and with flow the phi field) lives
+ * but the reduction's scratch (block partials, results, and for flow or 2D lattices the phi
+ * field) lives
  * in a file-scope device array of 4 MiB that every GPU loading this library holds until
- * the process exits. Lattices whose scratch exceeds 4 MiB (flow lattices above about one
- * million nodes) are rejected with LBM_ERR_ARG. The call allocates nothing. The first call
+ * the process exits. Lattices whose scratch exceeds 4 MiB (flow or 2D lattices above about
+ * one million nodes) are rejected with LBM_ERR_ARG. The call allocates nothing. The first call
  * on each device looks up the array's device address (cudaGetSymbolAddress) with that
  * device current; make that first call before any stream capture. Every call shares the
  * array and leaves its contents behind; the kernels overwrite all of it that they read, so
