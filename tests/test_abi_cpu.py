@@ -76,3 +76,17 @@ def test_sizes_and_validation_on_the_host(lib):
                           ctypes.c_void_p(8), ctypes.c_void_p(8), None, ctypes.byref(ctx))
         assert st == _lib.LBM_ERR_ARG
         assert field.encode() in lib.lbm_last_error(None)
+
+
+def test_header_is_plain_c99(tmp_path):
+    # the boundary is a C ABI: the header, and a C caller of it, compile as C99 with warnings
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    cuda_inc = "/usr/local/cuda/include"
+    out = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                          "-I", cuda_inc, "-c", os.path.join(ROOT, "tests", "c_abi_example.c"),
+                          "-o", str(tmp_path / "c_abi_example.o")], capture_output=True, text=True)
+    assert out.returncode == 0, out.stderr
