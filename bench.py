@@ -349,6 +349,18 @@ def gb300(args):
                                 "roofline_frac": b19 * nodes / (vms / vs / 1e3) / 1e9 / peak}
         del v
         torch.cuda.synchronize()
+        # 3D ripening without flow (256^3, D3Q7, FP32, in place): 21 populations, 168 B/node
+        from workloads import configs
+        p3, f3 = configs.ripening()
+        v = Simulation(p3, *f3(device=device), device=device)
+        vs = max(20, args.steps // 2)
+        vms, _, _ = time_device(v, vs, args.warmup, dist)
+        b3 = 2 * 21 * 4.0
+        var["ripening_3d"] = {"value": ws * p3.nodes * vs / (vms / 1e3) / 1e6, "unit": "MLUPS",
+                              "ms_per_step": vms / vs, "workload": "256^3 D3Q7, no flow, fraction 0.15, FP32, in place",
+                              "alg_bytes_per_node": b3, "roofline_frac": b3 * p3.nodes / (vms / vs / 1e3) / 1e9 / peak}
+        del v
+        torch.cuda.synchronize()
         # 2D ripening without flow on D2Q9 (§4.2.2 table): 4096^2, 27 FP32 populations in place,
         # with the one-pass droplet count and mean radius of Eq. 67 after the timed steps
         from workloads import configs
