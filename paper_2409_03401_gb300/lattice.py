@@ -66,6 +66,25 @@ class Simulation:
                                        ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self._ctx)))
         return self
 
+    def save(self, path):
+        """Checkpoint: the parameters, the time level and the raw state bytes (on the host)."""
+        torch.cuda.synchronize(self.device)
+        torch.save({"params": self.params.as_dict(), "t": self.t, "state": self.state.cpu()}, path)
+
+    @classmethod
+    def load(cls, path, device=None, stream=None):
+        """Resume a checkpoint written by ``save`` (same build of the library)."""
+        from workloads.params import LBMParams
+        ck = torch.load(path, map_location="cpu")
+        d = dict(ck["params"])
+        for key in ("c_eq", "M"):
+            d[key] = tuple(tuple(r) for r in d[key])
+        d["g"] = tuple(d["g"])
+        params = LBMParams(**d)
+        device = torch.device(device or "cuda")
+        state = ck["state"].to(device)
+        return cls.attach(params, state, ck["t"], device=device, stream=stream)
+
     @property
     def t(self):
         return int(self.lib.lbm_time(self._ctx))
