@@ -59,6 +59,20 @@ def test_adjoint_d3q19_scalar_lattice():
     assert float((gphi - gphi_ref).abs().max() / gphi_ref.abs().max()) <= 1e-8
 
 
+def test_adjoint_d2q9_lattice():
+    # the reverse mode on the 2D D2Q9 lattice (FP64 storage, periodic)
+    steps, K = 14, 6
+    p, fields = configs.ripening_2d(shape=(1, 40, 56), storage="f64", seed=12)
+    phi0, cA0, cB0 = fields()
+    target = oracle_adjoint.target_fields(p, configs.THETA_TARGET, phi0, cA0, cB0, steps)
+    L_ref, gth_ref, gphi_ref = oracle_adjoint.misfit_gradient(p, configs.THETA_EVAL, phi0, cA0, cB0, steps, target)
+    L, gth, gphi = _gpu_grad(p, phi0, cA0, cB0, steps, (target["phi"], target["muA"], target["muB"]), K)
+    assert abs(L - L_ref) <= 1e-9 * abs(L_ref)
+    assert float((gth - gth_ref).abs().max() / gth_ref.abs().max()) <= 1e-9
+    gphi = gphi.double().cpu()
+    assert float((gphi - gphi_ref).abs().max() / gphi_ref.abs().max()) <= 1e-8
+
+
 def test_gradient_vanishes_at_target_parameters():
     from paper_2409_03401_gb300.adjoint import forward_fields
     steps = 30
