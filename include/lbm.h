@@ -147,6 +147,15 @@ lbm_status lbm_attach(const lbm_params* p, void* d_state, void* d_work, int64_t 
 lbm_status lbm_step(lbm_ctx* ctx, int nsteps);
 
 /* Current time level (number of steps since lbm_init). */
+/* Advance nsteps coupled time steps by replaying a CUDA graph of two steps (captured on the
+ * first call from an even time level, after one plain pair of steps; kept until
+ * lbm_destroy): the same kernels and results as lbm_step, bit for bit, with one launch per
+ * two steps, for lattices small enough that launch overhead shows. The context's stream must
+ * be one the caller created (the legacy and per-thread default streams cannot be captured:
+ * LBM_ERR_ARG). The replayed graph holds the buffers bound at lbm_init/lbm_attach; steps run
+ * this way are not recorded by lbm_profile_begin. No counterpart in the paper. */
+lbm_status lbm_step_graph(lbm_ctx* ctx, int nsteps);
+
 int64_t lbm_time(const lbm_ctx* ctx);
 
 /* Macroscopic fields of the current time level into caller device buffers:

@@ -63,6 +63,7 @@ def load():
         "lbm_init": (ctypes.c_int, [P, vp, vp, vp, vp, vp, vp, ctx_pp]),
         "lbm_attach": (ctypes.c_int, [P, vp, vp, ctypes.c_int64, vp, ctx_pp]),
         "lbm_step": (ctypes.c_int, [vp, ctypes.c_int]),
+        "lbm_step_graph": (ctypes.c_int, [vp, ctypes.c_int]),
         "lbm_time": (ctypes.c_int64, [vp]),
         "lbm_fields": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_void_p)]),
         "lbm_reduce": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double)]),
@@ -95,7 +96,7 @@ def load():
 
 def exported_symbols():
     """Names of the C-ABI entry points this binding expects."""
-    return ["lbm_state_bytes", "lbm_work_bytes", "lbm_init", "lbm_attach", "lbm_step", "lbm_time",
+    return ["lbm_state_bytes", "lbm_work_bytes", "lbm_init", "lbm_attach", "lbm_step", "lbm_step_graph", "lbm_time",
             "lbm_fields", "lbm_reduce", "lbm_profile_begin", "lbm_profile_end", "lbm_kernels_per_step",
             "lbm_copy_bytes", "lbm_step_buffers", "lbm_adjoint_bytes", "lbm_adjoint_work_bytes",
             "lbm_adjoint_reset", "lbm_adjoint_seed", "lbm_adjoint_step", "lbm_adjoint_segment", "lbm_adjoint_init",

@@ -152,6 +152,7 @@ struct lbm_ctx {
     std::string err;
     std::vector<cudaEvent_t> ev;   // profiling: 3 events per timed step
     int prof_max = 0, prof_n = 0;
+    cudaGraphExec_t graph = nullptr;   // two steps captured from an even time level
 };
 
 namespace {
@@ -293,34 +294,78 @@ lbm_status lbm_attach(const lbm_params* p, void* d_state, void* d_work, int64_t 
     return s;
 }
 
+namespace {
+// Queue the kernels that advance time level t to t + 1 (no change to the context).
+void launch_one(lbm_ctx* c, int64_t t, cudaEvent_t* e) {
+    const int mode = c->L.two ? lbm::kModePull : ((t & 1) ? lbm::kModeAAOdd : lbm::kModeAAEven);
+    if (e) cudaEventRecord(e[0], c->stream);
+    // src holds time level t; dst receives t + 1 (the same buffer in the in-place layout)
+    const StateView& src = (c->L.two && (t & 1)) ? c->st1 : c->st;
+    const StateView& dst = c->L.two ? ((t & 1) ? c->st : c->st1) : c->st;
+    const bool fused = c->L.two && fused_flow(&c->p);
+    if (c->p.flow && !fused) {
+        LBM_DISPATCH(c->p.storage, launch_phi, c->dp, src, c->p.lattice, mode, c->work + c->L.off_phi, c->stream);
+    }
+    if (e) cudaEventRecord(e[1], c->stream);
+    if (fused) {
+        LBM_DISPATCH(c->p.storage, launch_fused, c->dp, src, dst, zchunk_of(&c->p), c->stream);
+    } else {
+        LBM_DISPATCH(c->p.storage, launch_step, c->dp, src, dst, c->p.lattice, c->p.flow != 0, mode,
+                     c->work + c->L.off_phi, c->stream);
+    }
+    if (e) cudaEventRecord(e[2], c->stream);
+}
+}  // namespace
+
 lbm_status lbm_step(lbm_ctx* c, int nsteps) {
     if (!c) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
     if (nsteps < 0) return fail(c, LBM_ERR_ARG, "nsteps must be >= 0");
     cudaGetLastError();
     for (int i = 0; i < nsteps; ++i) {
-        const int mode = read_mode(c);
         const bool timed = c->prof_n < c->prof_max;
-        cudaEvent_t* e = timed ? &c->ev[3 * c->prof_n] : nullptr;
-        if (timed) cudaEventRecord(e[0], c->stream);
-        // src holds time level t; dst receives t + 1 (the same buffer in the in-place layout)
-        const StateView& src = current(c);
-        const StateView& dst = c->L.two ? ((c->t & 1) ? c->st : c->st1) : c->st;
-        const bool fused = c->L.two && fused_flow(&c->p);
-        if (c->p.flow && !fused) {
-            LBM_DISPATCH(c->p.storage, launch_phi, c->dp, src, c->p.lattice, mode, c->work + c->L.off_phi,
-                         c->stream);
-        }
-        if (timed) cudaEventRecord(e[1], c->stream);
-        if (fused) {
-            LBM_DISPATCH(c->p.storage, launch_fused, c->dp, src, dst, zchunk_of(&c->p), c->stream);
-        } else {
-            LBM_DISPATCH(c->p.storage, launch_step, c->dp, src, dst, c->p.lattice, c->p.flow != 0, mode,
-                         c->work + c->L.off_phi, c->stream);
-        }
-        if (timed) { cudaEventRecord(e[2], c->stream); c->prof_n += 1; }
+        launch_one(c, c->t, timed ? &c->ev[3 * c->prof_n] : nullptr);
+        if (timed) c->prof_n += 1;
         c->t += 1;
     }
     return cuda_check(c, "step kernel launch");
+}
+
+lbm_status lbm_step_graph(lbm_ctx* c, int nsteps) {
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+    if (nsteps < 0) return fail(c, LBM_ERR_ARG, "nsteps must be >= 0");
+    if (c->stream == nullptr || c->stream == cudaStreamLegacy || c->stream == cudaStreamPerThread)
+        return fail(c, LBM_ERR_ARG, "graph replay needs a created (capturable) stream, not a default stream");
+    if (nsteps == 0) return LBM_OK;
+    if (c->t & 1) {                                  // align to an even time level
+        lbm_status s = lbm_step(c, 1);
+        if (s != LBM_OK || --nsteps == 0) return s;
+    }
+    if (!c->graph && nsteps >= 2) {
+        // one plain pair of steps first: every kernel's one-time set-up happens outside capture
+        lbm_status s = lbm_step(c, 2);
+        if (s != LBM_OK) return s;
+        nsteps -= 2;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            launch_one(c, c->t, nullptr);
+            launch_one(c, c->t + 1, nullptr);
+            e = cudaStreamEndCapture(c->stream, &g);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            c->graph = nullptr;
+            cudaGetLastError();
+            return fail(c, LBM_ERR_CUDA, std::string("step graph capture: ") + cudaGetErrorString(e));
+        }
+    }
+    for (; nsteps >= 2; nsteps -= 2) {
+        cudaError_t e = cudaGraphLaunch(c->graph, c->stream);
+        if (e != cudaSuccess) return fail(c, LBM_ERR_CUDA, std::string("step graph launch: ") + cudaGetErrorString(e));
+        c->t += 2;
+    }
+    return nsteps ? lbm_step(c, 1) : cuda_check(c, "step graph");
 }
 
 lbm_status lbm_profile_begin(lbm_ctx* c, int max_steps) {
@@ -531,6 +576,7 @@ lbm_status lbm_adjoint_theta(const lbm_params* p, void* d_adj_work, double* out,
 
 lbm_status lbm_destroy(lbm_ctx* c) {
     if (c) for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    if (c && c->graph) cudaGraphExecDestroy(c->graph);
     delete c;
     return LBM_OK;
 }

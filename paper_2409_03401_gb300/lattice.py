@@ -93,8 +93,11 @@ class Simulation:
     def real_dtype(self):
         return torch.float64 if self.params.storage == "f64" else torch.float32
 
-    def step(self, n=1):
-        _lib.check(self.lib.lbm_step(self._ctx, int(n)), self._ctx)
+    def step(self, n=1, graph=False):
+        """Advance n steps; ``graph=True`` replays a captured CUDA graph of two steps (needs a
+        created stream, e.g. Simulation(..., stream=torch.cuda.Stream()))."""
+        fn = self.lib.lbm_step_graph if graph else self.lib.lbm_step
+        _lib.check(fn(self._ctx, int(n)), self._ctx)
         return self
 
     def fields(self, names=_lib.FIELDS):

@@ -1,0 +1,69 @@
+"""lbm_step_graph: replaying a captured CUDA graph of two steps gives the same fields, bit for
+bit, as plain lbm_step launches (fused two-buffer flow, in-place AA without flow, and the
+D3Q19 phi pass + pull step), from even and odd time levels; and on the launch-bound
+512 x 8 diffusion couple it removes most of the per-step launch cost."""
+import time
+
+import pytest
+import torch
+
+from workloads import configs
+
+pytestmark = pytest.mark.gpu
+
+
+def _cases():
+    p1, f1 = configs.sedimentation(shape=(20, 24, 40), fraction=0.05, r=(3.0, 5.0))
+    p2, f2 = configs.ripening(shape=(12, 14, 33))
+    p3, f3 = configs.sedimentation(shape=(14, 18, 30), fraction=0.05, r=(3.0, 5.0))
+    return {"fused_flow": (p1, f1), "aa_noflow": (p2, f2), "d3q19_flow": (p3.with_(lattice="D3Q19"), f3)}
+
+
+@pytest.mark.parametrize("case", ["fused_flow", "aa_noflow", "d3q19_flow"])
+@pytest.mark.parametrize("first", [0, 1])
+def test_graph_replay_is_bit_identical(case, first):
+    from paper_2409_03401_gb300 import Simulation
+    p, fields = _cases()[case]
+    f = [t.cuda() for t in fields()]
+    s = torch.cuda.Stream()
+    a = Simulation(p, *f, stream=s)
+    b = Simulation(p, *f, stream=s)
+    a.step(first + 37)
+    b.step(first)
+    b.step(37, graph=True)
+    b.step(4, graph=True)               # replays the graph captured by the call above
+    a.step(4)
+    torch.cuda.synchronize()
+    assert a.t == b.t == first + 41
+    fa, fb = a.fields(), b.fields()
+    torch.cuda.synchronize()
+    for k in fa:
+        assert torch.equal(fa[k], fb[k]), k
+
+
+def test_graph_needs_a_created_stream():
+    from paper_2409_03401_gb300 import LBMError, Simulation
+    p, fields = configs.ripening(shape=(8, 8, 8))
+    sim = Simulation(p, *[t.cuda() for t in fields()])   # torch's default stream
+    if sim.stream.cuda_stream != 0:
+        pytest.skip("the current stream is not the legacy default stream")
+    with pytest.raises(LBMError):
+        sim.step(4, graph=True)
+
+
+def test_graph_on_the_launch_bound_couple():
+    from paper_2409_03401_gb300 import Simulation
+    p, fields = configs.diffusion_couple(storage="f64")
+    f = [t.cuda() for t in fields()]
+    s = torch.cuda.Stream()
+    times = {}
+    for graph in (False, True):
+        sim = Simulation(p, *f, stream=s)
+        sim.step(200, graph=graph)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.step(4000, graph=graph)
+        torch.cuda.synchronize()
+        times[graph] = (time.perf_counter() - t0) / 4000 * 1e6
+    print(f"512 x 8 couple, FP64: {times[False]:.2f} us/step plain, {times[True]:.2f} us/step graph")
+    assert times[True] < times[False]
