@@ -44,6 +44,23 @@ def _col(vals):
     return torch.tensor(vals, dtype=torch.float64).reshape(-1, 1, 1, 1)
 
 
+def _mrt_matrix():
+    """Rows of d'Humieres' D3Q19 moment basis evaluated on the D3Q19 velocities: density,
+    energy, energy square, (momentum, energy flux) per axis, (3 p_xx, pi_xx), (p_ww, pi_ww),
+    p_xy, p_yz, p_xz, m_x, m_y, m_z."""
+    rows = []
+    for k in range(D3Q19.Q):
+        cx, cy, cz = D3Q19.e[k]
+        c2 = cx * cx + cy * cy + cz * cz
+        rows.append([1.0, 19.0 * c2 - 30.0, (21.0 * c2 * c2 - 53.0 * c2 + 24.0) / 2.0,
+                     cx, (5.0 * c2 - 9.0) * cx, cy, (5.0 * c2 - 9.0) * cy, cz, (5.0 * c2 - 9.0) * cz,
+                     3.0 * cx * cx - c2, (3.0 * c2 - 5.0) * (3.0 * cx * cx - c2),
+                     cy * cy - cz * cz, (3.0 * c2 - 5.0) * (cy * cy - cz * cz),
+                     cx * cy, cy * cz, cx * cz,
+                     (cy * cy - cz * cz) * cx, (cz * cz - cx * cx) * cy, (cx * cx - cy * cy) * cz])
+    return [list(r) for r in zip(*rows)]
+
+
 class OracleLBM:
     """FP64 state of f (D3Q19, flow only), g, h^A, h^B and the step that advances it.
 
@@ -248,6 +265,24 @@ class OracleLBM:
         odd = 0.5 * (d - d_bar)
         return f - om_plus * even - om_minus * odd + Fk
 
+    def _mrt(self, f, f_eq, Fk, om_nu):
+        """Multiple-relaxation-time collision of the flow populations (the MRT operator the
+        paper names as an alternative to BGK, §3), on d'Humieres' orthogonal D3Q19 moment
+        basis: the moments of f - f^eq relax at their own rates, f* = f - M^-1 S M (f - f^eq)
+        + F_k. The shear moments (3p_xx, p_ww, p_xy, p_yz, p_xz) relax at omega_nu of Eq. 36
+        (they set nu); energy, energy square, energy flux, the fourth-order pi and the third-
+        order m moments at the rates of ``mrt_rates`` = (s_e, s_eps, s_q, s_pi, s_m); the
+        conserved density and momentum carry no non-equilibrium part. f^eq keeps the -F_k/2 of
+        Eq. 39 and F_k is added as in Eq. 36; M^-1 = M^T diag(1 / |row|^2)."""
+        M = torch.tensor(_mrt_matrix(), dtype=torch.float64)
+        norms = (M * M).sum(1)
+        s_e, s_eps, s_q, s_pi, s_m = self.p.mrt_rates
+        rates = torch.tensor([om_nu, s_e, s_eps, om_nu, s_q, om_nu, s_q, om_nu, s_q, om_nu, s_pi, om_nu, s_pi,
+                              om_nu, om_nu, om_nu, s_m, s_m, s_m], dtype=torch.float64)
+        dm = torch.tensordot(M, f - f_eq, dims=1)
+        relax = torch.tensordot(M.T, (rates / norms).reshape(-1, 1, 1, 1) * dm, dims=1)
+        return f - relax + Fk
+
     # ---------------------------------------------------------------- step
     def step(self, n=1):
         for _ in range(n):
@@ -282,6 +317,8 @@ class OracleLBM:
             om_f = m.relaxation_rate(p.nu, D3Q19.cs2)
             if p.collision == "TRT":
                 f_post = self._trt(self.f, f_eq, Fk, om_f)
+            elif p.collision == "MRT":
+                f_post = self._mrt(self.f, f_eq, Fk, om_f)
             else:
                 f_post = self.f - om_f * (self.f - f_eq) + Fk
             self.f = self._stream(f_post, D3Q19)

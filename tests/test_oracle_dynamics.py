@@ -116,7 +116,7 @@ def test_mode_decay_rates(lattice):
     assert abs(rate / (0.12 * k * k) - 1) < 0.01
 
 
-@pytest.mark.parametrize("collision", ["BGK", "TRT"])
+@pytest.mark.parametrize("collision", ["BGK", "TRT", "MRT"])
 def test_shear_wave_decay(collision):
     # the shear mode decays at nu k^2 with either collision: omega+ alone sets nu
     n = 32
@@ -185,6 +185,40 @@ def test_trt_with_equal_rates_is_bgk():
     o.init(*fields())
     o.step(10)
     assert float((runs[0].f - o.f).abs().max()) > 1e-9
+
+
+def _flow_run(p, fields, steps=10):
+    o = OracleLBM(p)
+    o.init(*fields())
+    o.step(steps)
+    return o
+
+
+def test_mrt_reduces_to_bgk_and_trt():
+    # The MRT moments are each even or odd under k -> opp(k). With every rate equal to the
+    # BGK rate the MRT update is BGK; with the even moments at omega+ and the odd ones (energy
+    # flux, m) at the TRT omega- it is TRT. Both up to round-off on a droplet lattice with walls
+    # and forcing; generic rates give a different run.
+    p, fields = configs.sedimentation(shape=(12, 14, 16), fraction=0.05, r=(2.0, 3.0))
+    om = 1.0 / (3.0 * p.nu + 0.5)
+    bgk = _flow_run(p, fields)
+    mrt_bgk = _flow_run(p.with_(collision="MRT", mrt_rates=(om,) * 5), fields)
+    assert float((bgk.f - mrt_bgk.f).abs().max()) < 1e-15
+    lam = 3.0 / 16.0
+    om_m = 1.0 / (lam / (1.0 / om - 0.5) + 0.5)
+    trt = _flow_run(p.with_(collision="TRT", trt_magic=lam), fields)
+    mrt_trt = _flow_run(p.with_(collision="MRT", mrt_rates=(om, om, om_m, om, om_m)), fields)
+    assert float((trt.f - mrt_trt.f).abs().max()) < 1e-15
+    mrt = _flow_run(p.with_(collision="MRT"), fields)
+    assert float((mrt.f - bgk.f).abs().max()) > 1e-9
+
+
+def test_mrt_moment_basis_is_orthogonal():
+    from oracle.lbm import _mrt_matrix
+    M = torch.tensor(_mrt_matrix(), dtype=torch.float64)
+    G = M @ M.T
+    norms = [19, 2394, 252, 10, 40, 10, 40, 10, 40, 36, 72, 12, 24, 4, 4, 4, 8, 8, 8]
+    assert torch.equal(G, torch.diag(torch.tensor(norms, dtype=torch.float64)))
 
 
 @pytest.mark.parametrize("lattice", ["D2Q5", "D3Q7", "D3Q19", "D2Q9"])

@@ -10,13 +10,13 @@ M[pi][alpha] the scaled species mobility of component alpha in phase pi (the
 diffusivity of the bulk phase, §2.3), nu the kinematic viscosity, sigma the
 surface tension, g the buoyancy acceleration times the density contrast
 (F_g = phi * g, §2.5). collision selects the flow collision operator: the paper's BGK,
-or the two-relaxation-time operator it names as an alternative (§3).
+or the two- and multiple-relaxation-time operators it names as alternatives (§3).
 """
 from dataclasses import dataclass, field, asdict, replace
 from typing import Tuple
 
 LATTICES = ("D2Q5", "D3Q7", "D3Q19", "D2Q9")
-COLLISIONS = ("BGK", "TRT")
+COLLISIONS = ("BGK", "TRT", "MRT")
 STORAGES = ("f64", "f32", "f16", "bf16")
 
 
@@ -41,8 +41,10 @@ class LBMParams:
     sigma: float = 1.0e-3
     g: Tuple[float, float, float] = (0.0, 0.0, -1.0e-5)
     f_scale: float = 1024.0        # 16-bit storage: scale applied to f_k / w_k before rounding
-    collision: str = "BGK"         # flow collision: "BGK" (one rate) or "TRT" (two rates)
+    collision: str = "BGK"         # flow collision: "BGK" (one rate), "TRT" (two) or "MRT"
     trt_magic: float = 3.0 / 16.0  # TRT: Lambda = (1/omega+ - 1/2)(1/omega- - 1/2)
+    # MRT rates of the energy, energy-square, energy-flux, pi and m moments (d'Humieres 2002)
+    mrt_rates: Tuple[float, float, float, float, float] = (1.19, 1.4, 1.2, 1.4, 1.98)
 
     def __post_init__(self):
         if self.lattice not in LATTICES:
@@ -57,6 +59,8 @@ class LBMParams:
             raise ValueError(f"collision must be one of {COLLISIONS}")
         if not self.trt_magic > 0:
             raise ValueError("trt_magic must be > 0")
+        if len(self.mrt_rates) != 5 or not all(0 < r < 2 for r in self.mrt_rates):
+            raise ValueError("mrt_rates: five rates in (0, 2)")
         if self.flow and self.lattice in ("D2Q5", "D2Q9"):
             raise ValueError("flow is implemented on 3D lattices (D3Q19 flow + D3Q7 or D3Q19 scalars)")
 
