@@ -337,6 +337,16 @@ def gb300(args):
                       "roofline_frac": ALG_BYTES_PER_NODE["f32"] * nodes / (vstep / 1e3) / 1e9 / peak}
         del v
         torch.cuda.synchronize()
+        # the multiple-relaxation-time flow collision (D3Q19 moment basis), FP32 storage
+        q = p.with_(collision="MRT")
+        v = Simulation(q, *init, device=device)
+        vs = max(20, args.steps // 2)
+        vms, _, vstep = time_device(v, vs, args.warmup, dist)
+        var["mrt"] = {"value": ws * nodes * vs / (vms / 1e3) / 1e6, "unit": "MLUPS", "ms_per_step": vms / vs,
+                      "speedup_vs_f32": (ms / args.steps) / (vms / vs), "collision": "MRT, d'Humieres rates",
+                      "roofline_frac": ALG_BYTES_PER_NODE["f32"] * nodes / (vstep / 1e3) / 1e9 / peak}
+        del v
+        torch.cuda.synchronize()
         # D3Q19 for phi, c^A, c^B (the paper's lattice for every equation): 76 populations,
         # phi pass + per-node pull step, FP32 storage
         q = p.with_(lattice="D3Q19")

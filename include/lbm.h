@@ -58,11 +58,13 @@ typedef enum { LBM_D2Q5 = 0, LBM_D3Q7 = 1, LBM_D3Q19 = 2, LBM_D2Q9 = 3 } lbm_lat
 typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16 = 2, LBM_BF16 = 3 } lbm_storage;
 
 /* Model parameters in lattice units (dx = dt = 1, rho_0 = 1), named as in the paper. */
-/* Flow collision operators. LBM_BGK is the paper's single-rate operator (Eq. 36). LBM_TRT is
- * the two-relaxation-time operator the paper names as an alternative (§3): the parts of
- * f - f^eq even and odd under k -> opp(k) relax at omega+ and omega-; f^eq keeps the
- * -F_k/2 shift of Eq. 39 and F_k is added as in Eq. 36. */
-typedef enum { LBM_BGK = 0, LBM_TRT = 1 } lbm_collision;
+/* Flow collision operators. LBM_BGK is the paper's single-rate operator (Eq. 36). LBM_TRT and
+ * LBM_MRT are the two- and multiple-relaxation-time operators the paper names as
+ * alternatives (§3). TRT: the parts of f - f^eq even and odd under k -> opp(k) relax at
+ * omega+ and omega-. MRT: the moments of f - f^eq on d'Humieres' orthogonal D3Q19 basis relax
+ * at their own rates (shear moments at omega of Eq. 36). In both, f^eq keeps the -F_k/2 shift
+ * of Eq. 39 and F_k is added as in Eq. 36. */
+typedef enum { LBM_BGK = 0, LBM_TRT = 1, LBM_MRT = 2 } lbm_collision;
 
 typedef struct lbm_params {
     int32_t nx, ny, nz;      /* lattice extents; nz = 1 with LBM_D2Q5 */
@@ -88,6 +90,8 @@ typedef struct lbm_params {
     int32_t collision;       /* flow collision, lbm_collision: LBM_BGK (Eq. 36) or LBM_TRT */
     double trt_magic;        /* LBM_TRT: Lambda = (1/omega+ - 1/2)(1/omega- - 1/2) > 0, where omega+
                               * is the BGK rate of Eq. 36 (it sets nu); 0 selects 3/16 */
+    double mrt_rates[5];     /* LBM_MRT: rates in (0, 2) of the energy, energy-square, energy-flux,
+                              * pi and m moments; 0 selects 1.19, 1.4, 1.2, 1.4, 1.98 */
 } lbm_params;
 
 /* Indices of lbm_fields outputs. */

@@ -14,8 +14,8 @@ LBM_D2Q5, LBM_D3Q7, LBM_D3Q19, LBM_D2Q9 = 0, 1, 2, 3
 LBM_F64, LBM_F32, LBM_F16, LBM_BF16 = 0, 1, 2, 3
 STORAGE = {"f64": LBM_F64, "f32": LBM_F32, "f16": LBM_F16, "bf16": LBM_BF16}
 LATTICE = {"D2Q5": LBM_D2Q5, "D3Q7": LBM_D3Q7, "D3Q19": LBM_D3Q19, "D2Q9": LBM_D2Q9}
-LBM_BGK, LBM_TRT = 0, 1
-COLLISION = {"BGK": LBM_BGK, "TRT": LBM_TRT}
+LBM_BGK, LBM_TRT, LBM_MRT = 0, 1, 2
+COLLISION = {"BGK": LBM_BGK, "TRT": LBM_TRT, "MRT": LBM_MRT}
 FIELDS = ("phi", "muA", "muB", "cA", "cB", "p", "ux", "uy", "uz", "S")
 REDUCTIONS = ("phi", "cA", "cB", "p", "S", "umax", "g", "nonfinite", "interface", "euler")
 NFIELDS = len(FIELDS)
@@ -32,7 +32,7 @@ class lbm_params(ctypes.Structure):
         ("c_eq", (ctypes.c_double * 2) * 2), ("M", (ctypes.c_double * 2) * 2),
         ("nu", ctypes.c_double), ("sigma", ctypes.c_double), ("g", ctypes.c_double * 3),
         ("f_scale", ctypes.c_double),
-        ("collision", ctypes.c_int32), ("trt_magic", ctypes.c_double),
+        ("collision", ctypes.c_int32), ("trt_magic", ctypes.c_double), ("mrt_rates", ctypes.c_double * 5),
     ]
 
 
@@ -130,4 +130,6 @@ def make_params(p):
     c.f_scale = p.f_scale
     c.collision = COLLISION[p.collision]
     c.trt_magic = p.trt_magic
+    for i, r in enumerate(p.mrt_rates):
+        c.mrt_rates[i] = r
     return c

@@ -58,7 +58,10 @@ const char* check_params(const lbm_params* p) {
             if (!(p->M[ph][a] > 0)) return "mobilities M must be > 0";
     if (p->flow && !(p->nu > 0)) return "nu must be > 0 with flow";
     if (!(p->f_scale == 0.0 || p->f_scale == 1024.0)) return "f_scale must be 0 or 1024 (the fixed 16-bit scale)";
-    if (p->collision != LBM_BGK && p->collision != LBM_TRT) return "collision must be LBM_BGK or LBM_TRT";
+    if (p->collision != LBM_BGK && p->collision != LBM_TRT && p->collision != LBM_MRT)
+        return "collision must be LBM_BGK, LBM_TRT or LBM_MRT";
+    for (int i = 0; i < 5; ++i)
+        if (!(p->mrt_rates[i] >= 0 && p->mrt_rates[i] < 2)) return "mrt_rates must lie in [0, 2) (0 selects the default)";
     if (p->collision == LBM_TRT && !(p->trt_magic >= 0)) return "trt_magic must be >= 0 (0 selects 3/16)";
     return nullptr;
 }
@@ -102,6 +105,7 @@ void fill_coef(const DevParams& d, lbm::Coef<R>& c) {
     c.om_g = R(d.om_g);
     c.om_f = R(d.om_f);
     c.om_fm = R(d.om_fm);
+    for (int i = 0; i < 19; ++i) c.mrt[i] = R(d.mrt[i]);
     c.sw15 = R(d.sw15);
     c.inv_W2 = R(d.inv_W2);
     for (int i = 0; i < 3; ++i) c.g[i] = R(d.g[i]);
@@ -125,9 +129,16 @@ DevParams dev_params(const lbm_params* p, const Layout& L) {
     }
     d.om_g = 1.0 / (p->M_phi / cs2 + 0.5);
     d.om_f = p->flow ? 1.0 / (p->nu * 3.0 + 0.5) : 0.0;
-    d.trt = p->flow && p->collision == LBM_TRT;
+    d.coll = p->flow ? p->collision : LBM_BGK;
     const double magic = p->trt_magic > 0 ? p->trt_magic : 3.0 / 16.0;
-    d.om_fm = d.trt ? 1.0 / (magic / (p->nu * 3.0) + 0.5) : d.om_f;
+    d.om_fm = d.coll == LBM_TRT ? 1.0 / (magic / (p->nu * 3.0) + 0.5) : d.om_f;
+    // MRT rates per moment: shear moments at om_f, the others from mrt_rates (0 = default)
+    const double def[5] = {1.19, 1.4, 1.2, 1.4, 1.98};
+    double r[5];
+    for (int i = 0; i < 5; ++i) r[i] = p->mrt_rates[i] > 0 ? p->mrt_rates[i] : def[i];
+    const double rate[19] = {d.om_f, r[0], r[1], d.om_f, r[2], d.om_f, r[2], d.om_f, r[2], d.om_f, r[3],
+                             d.om_f, r[3], d.om_f, d.om_f, d.om_f, r[4], r[4], r[4]};
+    for (int i = 0; i < 19; ++i) d.mrt[i] = rate[i] / lbm::MRT19::norm(i);
     d.sw15 = 1.5 * p->sigma * p->W;
     d.inv_W2 = 1.0 / (p->W * p->W);
     for (int i = 0; i < 3; ++i) d.g[i] = p->g[i];

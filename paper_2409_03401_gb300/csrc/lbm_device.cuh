@@ -17,12 +17,13 @@ namespace lbm {
 template <class R>
 struct Coef {
     R lam, kphi, c0[2], dc[2], om_g, M0[2], M1[2], om_f, om_fm, sw15, inv_W2, g[3];
+    R mrt[19];            // MRT: rate / |row|^2 of each moment of the D3Q19 basis
 };
 
 struct DevParams {
     int nx, ny, nz;
     int wall_x, wall_z, source_off;
-    int trt;              // flow collision: 0 BGK (Eq. 36), 1 two-relaxation-time
+    int coll;             // flow collision: 0 BGK (Eq. 36), 1 TRT, 2 MRT
     long long n;          // nodes
     long long plane;      // elements between two population planes (n rounded up)
     double W, lam;
@@ -34,6 +35,7 @@ struct DevParams {
     double inv_cs2;       // 1 / c_s^2 of the scalar lattice
     double om_f;          // 1 / (nu / c_s^2 + 1/2)  (Eq. 36), c_s^2 = 1/3
     double om_fm;         // TRT rate of the odd part: 1 / (Lambda / (1/om_f - 1/2) + 1/2)
+    double mrt[19];       // MRT rate of each moment divided by the squared norm of its row
     double sw15;          // (3/2) sigma W  (Eq. 34)
     double inv_W2;
     double g[3];          // buoyancy per unit phi
@@ -107,6 +109,42 @@ struct D3Q19 {
 };
 
 __host__ __device__ constexpr int opp(int k) { return k == 0 ? 0 : ((k & 1) ? k + 1 : k - 1); }
+
+// d'Humieres' orthogonal moment basis of D3Q19, evaluated on the velocities above: row i
+// is density, energy, energy square, (momentum, energy flux) per axis, (3 p_xx, pi_xx),
+// (p_ww, pi_ww), p_xy, p_yz, p_xz, m_x, m_y, m_z. Rows are orthogonal; norm(i) = |row i|^2.
+struct MRT19 {
+    __host__ __device__ static constexpr double m(int i, int k) {
+        const double cx = D3Q19::ex(k), cy = D3Q19::ey(k), cz = D3Q19::ez(k);
+        const double c2 = cx * cx + cy * cy + cz * cz;
+        switch (i) {
+            case 0: return 1.0;
+            case 1: return 19.0 * c2 - 30.0;
+            case 2: return (21.0 * c2 * c2 - 53.0 * c2 + 24.0) / 2.0;
+            case 3: return cx;
+            case 4: return (5.0 * c2 - 9.0) * cx;
+            case 5: return cy;
+            case 6: return (5.0 * c2 - 9.0) * cy;
+            case 7: return cz;
+            case 8: return (5.0 * c2 - 9.0) * cz;
+            case 9: return 3.0 * cx * cx - c2;
+            case 10: return (3.0 * c2 - 5.0) * (3.0 * cx * cx - c2);
+            case 11: return cy * cy - cz * cz;
+            case 12: return (3.0 * c2 - 5.0) * (cy * cy - cz * cz);
+            case 13: return cx * cy;
+            case 14: return cy * cz;
+            case 15: return cx * cz;
+            case 16: return (cy * cy - cz * cz) * cx;
+            case 17: return (cz * cz - cx * cx) * cy;
+            default: return (cx * cx - cy * cy) * cz;
+        }
+    }
+    __host__ __device__ static constexpr double norm(int i) {
+        double s = 0.0;
+        for (int k = 0; k < 19; ++k) s += m(i, k) * m(i, k);
+        return s;
+    }
+};
 
 // D3Q19 as the lattice of phi, c^A, c^B: the paper's choice for every equation (§3).
 template <> struct Scalar<LAT_D3Q19> {

@@ -254,7 +254,35 @@ __device__ __forceinline__ R edot(int ex, int ey, int ez, R vx, R vy, R vz) {
 // every term above carries the factor w_k, so dividing it out leaves the same affine update
 // on q with the per-direction weights gone, e.g. q*_f = q - om (q - s E_k) + s G_k with
 // E_k = f^eq / w, G_k = F_k / w, s = kFScale.
-template <class T, int LAT, bool FLOW, class A>
+// COLL: flow collision fixed at compile time (0 BGK, 1 TRT, 2 MRT); -1 reads P.coll to
+// choose between BGK and TRT only, -2 reads it to choose among all three.
+// MRT on the D3Q19 moment basis: d = f - f^eq, dm_i = (rate_i / |M_i|^2) sum_k M_ik d_k,
+// f*_k = f_k - sum_i M_ik dm_i + F_k (M^-1 = M^T diag(1 / |M_i|^2)).
+template <class R, class Pre, class Post>
+__device__ __forceinline__ void mrt_relax(const DevParams& P, Pre d_of, Post put) {
+    R d[19];
+#pragma unroll
+    for (int k = 0; k < 19; ++k) d[k] = d_of(k);
+    R dm[19];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        R a = R(0);
+#pragma unroll
+        for (int k = 0; k < 19; ++k)
+            if (MRT19::m(i, k) != 0.0) a += R(MRT19::m(i, k)) * d[k];
+        dm[i] = a * coef<R>(P).mrt[i];
+    }
+#pragma unroll
+    for (int k = 0; k < 19; ++k) {
+        R r = R(0);
+#pragma unroll
+        for (int i = 0; i < 19; ++i)
+            if (MRT19::m(i, k) != 0.0) r += R(MRT19::m(i, k)) * dm[i];
+        put(k, r);
+    }
+}
+
+template <class T, int LAT, bool FLOW, class A, int COLL = -2>
 __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, typename RealOf<T>::type phi,
                                               typename RealOf<T>::type ux, typename RealOf<T>::type uy,
                                               typename RealOf<T>::type uz, typename RealOf<T>::type Fx,
@@ -291,13 +319,21 @@ __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, type
                 Fk = w * (Ac + cu * (R(3) + R(4.5) * cu)) * (edot(ex, ey, ez, Fx, Fy, Fz) - uF);
                 feq = w * (Bc + cu * (R(1) + R(1.5) * cu)) - R(0.5) * Fk;
             };
-            if (!P.trt) {                                     // BGK, Eq. 36
+            const int coll = COLL >= 0 ? COLL : (COLL == -1 && P.coll == 2 ? 0 : P.coll);
+            if (coll == 0) {                                  // BGK, Eq. 36
 #pragma unroll
                 for (int k = 0; k < 19; ++k) {
                     R Fk, feq;
                     force_eq_w(k, Fk, feq);
                     put(k, nd.f[k] - omf * (nd.f[k] - feq) + Fk);
                 }
+            } else if ((COLL == 2 || COLL == -2) && coll == 2) {   // multiple relaxation times
+                R Fs[19];
+                mrt_relax<R>(P, [&](int k) {
+                    R feq;
+                    force_eq_w(k, Fs[k], feq);
+                    return nd.f[k] - feq;
+                }, [&](int k, R r) { put(k, nd.f[k] - r + Fs[k]); });
             } else {                                          // two relaxation times
                 const R omm = coef<R>(P).om_fm;
                 R F0, feq0;
@@ -322,13 +358,29 @@ __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, type
                 stored += R(Codec<T>::template scale<SET_F>(D3Q19::w(k))) *
                           Codec<T>::store_q_back(element<T, 0>(out, k, sl), q);
             };
-            if (!P.trt) {
+            const int coll = COLL >= 0 ? COLL : (COLL == -1 && P.coll == 2 ? 0 : P.coll);
+            if (coll == 0) {
 #pragma unroll
                 for (int k = 1; k < 19; ++k) {
                     R G, E;
                     force_eq(k, G, E);
                     put(k, nd.f[k] - omf * (nd.f[k] - s * E) + s * G);
                 }
+            } else if ((COLL == 2 || COLL == -2) && coll == 2) {
+                // MRT mixes directions: run it on the populations in natural units
+                R Fs[19];
+                mrt_relax<R>(P, [&](int k) {
+                    R G, E;
+                    force_eq(k, G, E);
+                    const R w = R(D3Q19::w(k));
+                    Fs[k] = w * G;
+                    const R fk = k == 0 ? nd.f[0] : R(Codec<T>::template scale<SET_F>(D3Q19::w(k))) * nd.f[k];
+                    return fk - w * E;
+                }, [&](int k, R r) {
+                    if (k == 0) return;                      // the rest population is set below
+                    const R fk = R(Codec<T>::template scale<SET_F>(D3Q19::w(k))) * nd.f[k];
+                    put(k, (fk - r + Fs[k]) * R(1.0 / Codec<T>::template scale<SET_F>(D3Q19::w(k))));
+                });
             } else {
                 const R omm = coef<R>(P).om_fm;
 #pragma unroll
@@ -415,7 +467,7 @@ __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, type
 // ------------------------------------------------------------------------------------
 // One coupled step per node. With flow the phi field of this step must already be in
 // phi_field (phi pass); MODE AA_* works in place on ``st``, PULL reads ``st`` and writes ``out``.
-template <class T, int LAT, bool FLOW, int MODE>
+template <class T, int LAT, bool FLOW, int MODE, int COLL>
 __global__ void __launch_bounds__(kBlockX)
 step_kernel(const DevParams P, const StateView st, const StateView out,
             const typename RealOf<T>::type* __restrict__ phi_field) {
@@ -437,7 +489,7 @@ step_kernel(const DevParams P, const StateView st, const StateView out,
         stencil([&](int dx, int dy, int dz) { return ad.phi(phi_field, dx, dy, dz); }, phi, gx, gy, gz, lap);
         force_velocity(nd, phi, gx, gy, gz, lap, P, Fx, Fy, Fz, ux, uy, uz);
     }
-    collide_store(nd, phi, ux, uy, uz, Fx, Fy, Fz, out, ad, P);
+    collide_store<T, LAT, FLOW, Addr<MODE>, COLL>(nd, phi, ux, uy, uz, Fx, Fy, Fz, out, ad, P);
 }
 
 // phi = sum g + S/2 of every node (Eq. 49), read by the capillary stencil.
@@ -480,9 +532,14 @@ __host__ __device__ constexpr size_t fused_smem_bytes() {
     return sizeof(R) * (4 * (FY + 2) * (FX + 2) + 2 * kSPops * FT);
 }
 
-template <class T>
+// COLL: the flow collision of this instance. FP32/FP64 storage keeps BGK and TRT in one
+// instance behind a block-uniform branch on P.coll (measured 1 % faster for BGK than a
+// BGK-only instance at this register budget); 16-bit storage and MRT get instances of their
+// own (the 16-bit BGK instance is 6 % faster without the TRT code).
+template <class T, int COLL>
 __global__ void __launch_bounds__(FT, sizeof(typename RealOf<T>::type) == 8 ? 1 : 3)
 fused_flow_kernel(const DevParams P, const StateView src, const StateView dst, int zchunk) {
+    constexpr int kColl = (!is16<T>() && COLL != 2) ? -1 : COLL;
     using R = typename RealOf<T>::type;
     using L = Scalar<LAT_D3Q7>;
     constexpr int Q = L::Q;
@@ -609,7 +666,8 @@ fused_flow_kernel(const DevParams P, const StateView src, const StateView dst, i
                     return ring[s][ty + 1 + dy][tx + 1 + dx];
                 }, phi, gx, gy, gz, lap);
         force_velocity(nd, phi, gx, gy, gz, lap, P, Fx, Fy, Fz, ux, uy, uz);
-        collide_store(nd, phi, ux, uy, uz, Fx, Fy, Fz, dst, ad, P);
+        collide_store<T, LAT_D3Q7, true, std::decay_t<decltype(ad)>, kColl>(nd, phi, ux, uy, uz, Fx, Fy, Fz, dst,
+                                                                            ad, P);
     };
 
     fill_any(zs - 1, (zs - 1) & 3, -1);
@@ -847,22 +905,45 @@ struct Launchers {
                      cudaStream_t s) {
         int bx; const dim3 grid = node_grid(P, bx);
         R* phi = static_cast<R*>(phi_work);
-        LBM_MODE_SWITCH(mode, step_kernel<T, LAT, FLOW, M><<<grid, bx, 0, s>>>(P, st, out, phi));
+        // MRT in an instance of its own: its 19 x 19 transform would raise every instance's registers
+        if constexpr (FLOW) {
+            if (P.coll == 2) {
+                LBM_MODE_SWITCH(mode, step_kernel<T, LAT, FLOW, M, 2><<<grid, bx, 0, s>>>(P, st, out, phi));
+                return;
+            }
+        }
+        LBM_MODE_SWITCH(mode, step_kernel<T, LAT, FLOW, M, -1><<<grid, bx, 0, s>>>(P, st, out, phi));
     }
     static void fused(const DevParams& P, const StateView& src, const StateView& dst, int zchunk, cudaStream_t s) {
         const dim3 block(FX, FY);
         const dim3 grid((P.nx + FX - 1) / FX, (P.ny + FY - 1) / FY, (P.nz + zchunk - 1) / zchunk);
         constexpr size_t smem = fused_smem_bytes<T>();
+        // instances per flow collision (see fused_flow_kernel)
+        if (P.coll == 2) {
+            launch_fused_coll<2>(P, src, dst, zchunk, grid, block, smem, s);
+            return;
+        }
+        if constexpr (is16<T>()) {
+            if (P.coll == 1) {
+                launch_fused_coll<1>(P, src, dst, zchunk, grid, block, smem, s);
+                return;
+            }
+        }
+        launch_fused_coll<0>(P, src, dst, zchunk, grid, block, smem, s);
+    }
+    template <int COLL>
+    static void launch_fused_coll(const DevParams& P, const StateView& src, const StateView& dst, int zchunk,
+                                  dim3 grid, dim3 block, size_t smem, cudaStream_t s) {
         // opt in to more than 48 KB of dynamic shared memory, once per device (a repeated
         // call from a racing thread is harmless)
         static unsigned long long configured = 0;
         int dev = 0;
         cudaGetDevice(&dev);
         if (dev < 64 && !(configured & (1ull << dev))) {
-            cudaFuncSetAttribute(fused_flow_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+            cudaFuncSetAttribute(fused_flow_kernel<T, COLL>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
             configured |= 1ull << dev;
         }
-        fused_flow_kernel<T><<<grid, block, smem, s>>>(P, src, dst, zchunk);
+        fused_flow_kernel<T, COLL><<<grid, block, smem, s>>>(P, src, dst, zchunk);
     }
     template <int LAT, bool FLOW>
     static void fields(const DevParams& P, const StateView& st, int mode, void* phi_work, FieldPtrs out,

@@ -68,9 +68,12 @@ def test_sizes_and_validation_on_the_host(lib):
     # magic parameter is rejected before any device work
     trt = _lib.make_params(p.with_(collision="TRT"))
     assert lib.lbm_state_bytes(ctypes.byref(trt)) == state
-    for field, value in (("collision", 2), ("trt_magic", -1.0)):
+    for field, value in (("collision", 3), ("trt_magic", -1.0), ("mrt_rates", 2.5)):
         badc = _lib.make_params(p.with_(collision="TRT"))
-        setattr(badc, field, value)
+        if field == "mrt_rates":
+            badc.mrt_rates[2] = value
+        else:
+            setattr(badc, field, value)
         assert lib.lbm_state_bytes(ctypes.byref(badc)) == 0
         st = lib.lbm_init(ctypes.byref(badc), ctypes.c_void_p(256), ctypes.c_void_p(256), ctypes.c_void_p(8),
                           ctypes.c_void_p(8), ctypes.c_void_p(8), None, ctypes.byref(ctx))
