@@ -31,7 +31,7 @@ ALG_BYTES_PER_NODE = {"f32": 320.0, "f16": 176.0, "bf16": 176.0, "f64": 640.0}
 # DRAM bytes (read + write) per node of one fused_flow_kernel<float> launch, from an ncu capture
 # of this kernel at 192^3 (profiles/fused_flow_kernel_f32_192cube.md); traffic scales with the
 # node count. Set to None whenever the kernel changes until it is captured again.
-NCU_DRAM_BYTES_PER_NODE_F32 = 163.94 + 153.83
+NCU_DRAM_BYTES_PER_NODE_F32 = 164.06 + 153.78
 
 
 def parse():
@@ -300,7 +300,7 @@ def gb300(args):
                      "frac": achieved / peak,
                      "traffic": (None if NCU_DRAM_BYTES_PER_NODE_F32 is None or args.storage != "f32"
                                  else NCU_DRAM_BYTES_PER_NODE_F32 * nodes),
-                     "kernel": f"fused_flow_kernel<{'float' if args.storage == 'f32' else args.storage}> "
+                     "kernel": f"fused_flow_kernel<{'float' if args.storage == 'f32' else args.storage}, BGK> "
                                "(z-marching fused phi + collide + stream)",
                      "alg_bytes_per_launch": bytes_step, "ms_per_launch": ms_step,
                      "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
