@@ -31,7 +31,7 @@ ALG_BYTES_PER_NODE = {"f32": 320.0, "f16": 176.0, "bf16": 176.0, "f64": 640.0}
 # DRAM bytes (read + write) per node of one fused_flow_kernel<float> launch, from an ncu capture
 # of this kernel at 192^3 (profiles/fused_flow_kernel_f32_192cube.md); traffic scales with the
 # node count. Set to None whenever the kernel changes until it is captured again.
-NCU_DRAM_BYTES_PER_NODE_F32 = 164.06 + 153.78
+NCU_DRAM_BYTES_PER_NODE_F32 = 164.98 + 153.87
 
 
 def parse():

@@ -163,6 +163,23 @@ struct Node {
         const R pt = interp_p(phit);
         S = source(phit, closure_dev(dcA, pt, 0, P), closure_dev(dcB, pt, 1, P), P);
     }
+    // c - c_0^eq of both components (Eq. 52 with the shifted h_0), as in moments()
+    __device__ __forceinline__ void dc_sums() {
+        if constexpr (is16<T>()) {
+            using C = Codec<T>;
+            dcA = hA[0];
+            dcB = hB[0];
+#pragma unroll
+            for (int k = 1; k < Q; ++k) {
+                dcA += R(C::template scale<SET_H>(Scalar<LAT>::w(k))) * hA[k];
+                dcB += R(C::template scale<SET_H>(Scalar<LAT>::w(k))) * hB[k];
+            }
+        } else {
+            dcA = R(0); dcB = R(0);
+#pragma unroll
+            for (int k = 0; k < Q; ++k) { dcA += hA[k]; dcB += hB[k]; }
+        }
+    }
     // p_h = sum f (Eq. 40)
     __device__ __forceinline__ R flow_p() const {
         static_assert(FLOW, "flow moments of a node without flow populations");
@@ -524,12 +541,18 @@ phi_kernel(const DevParams P, const StateView st, typename RealOf<T>::type* __re
 // populations are read from HBM once; the halo re-reads hit L2.
 constexpr int FX = 32, FY = 8, FT = FX * FY;
 constexpr int kHalo = 2 * (FX + 2) + 2 * FY;    // ring positions outside the tile (84)
-constexpr int kSPops = 3 * 7 + 3;               // 21 scalar populations + S, dcA, dcB
+// Parked per tile node: 21 scalar populations and S, plus c - c_0^eq with 16-bit storage.
+// FP32/FP64 sum c - c_0^eq again from the parked h instead: the 4 KB saved per block let
+// three blocks fit the 164 KB shared-memory carveout, leaving 92 KB of L1 rather than 60 KB
+// for the gathers in flight (1.4 % faster); the instruction-bound 16-bit kernel parks it
+// (6 % faster than summing it again).
+template <class T> constexpr bool park_dc() { return is16<T>(); }
+template <class T> constexpr int spops_n() { return 3 * 7 + (park_dc<T>() ? 3 : 1); }
 
 template <class T>
 __host__ __device__ constexpr size_t fused_smem_bytes() {
     using R = typename RealOf<T>::type;
-    return sizeof(R) * (4 * (FY + 2) * (FX + 2) + 2 * kSPops * FT);
+    return sizeof(R) * (4 * (FY + 2) * (FX + 2) + 2 * spops_n<T>() * FT);
 }
 
 // COLL: the flow collision of this instance. FP32/FP64 storage keeps BGK and TRT in one
@@ -545,7 +568,9 @@ fused_flow_kernel(const DevParams P, const StateView src, const StateView dst, i
     constexpr int Q = L::Q;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R (*ring)[FY + 2][FX + 2] = reinterpret_cast<R (*)[FY + 2][FX + 2]>(smem_raw);
-    R* spops = reinterpret_cast<R*>(smem_raw) + 4 * (FY + 2) * (FX + 2);   // [2][kSPops][FT]
+    R* spops = reinterpret_cast<R*>(smem_raw) + 4 * (FY + 2) * (FX + 2);   // [2][spops_n][FT]
+    constexpr int kSPops = spops_n<T>();
+    constexpr bool kParkDc = park_dc<T>();
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * FX + tx;
     const int x0 = blockIdx.x * FX, y0 = blockIdx.y * FY;
@@ -615,8 +640,10 @@ fused_flow_kernel(const DevParams P, const StateView src, const StateView dst, i
                     sp[(2 * Q + k) * FT] = nd.hB[k];
                 }
                 sp[(3 * Q) * FT] = nd.S;
-                sp[(3 * Q + 1) * FT] = nd.dcA;
-                sp[(3 * Q + 2) * FT] = nd.dcB;
+                if constexpr (kParkDc) {
+                    sp[(3 * Q + 1) * FT] = nd.dcA;
+                    sp[(3 * Q + 2) * FT] = nd.dcB;
+                }
             }
         }
         ring[s][ty + 1][tx + 1] = v;
@@ -651,14 +678,17 @@ fused_flow_kernel(const DevParams P, const StateView src, const StateView dst, i
         nd.gather_flow(src, ad, P);
         const R* spc = spops + (z & 1) * kSPops * FT + tid;
         nd.S = spc[(3 * Q) * FT];
-        nd.dcA = spc[(3 * Q + 1) * FT];
-        nd.dcB = spc[(3 * Q + 2) * FT];
+        if constexpr (kParkDc) {
+            nd.dcA = spc[(3 * Q + 1) * FT];
+            nd.dcB = spc[(3 * Q + 2) * FT];
+        }
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
             nd.g[k] = spc[k * FT];
             nd.hA[k] = spc[(Q + k) * FT];
             nd.hB[k] = spc[(2 * Q + k) * FT];
         }
+        if constexpr (!kParkDc) nd.dc_sums();
         const R phi = ring[sc][ty + 1][tx + 1];
         R gx, gy, gz, lap, Fx, Fy, Fz, ux, uy, uz;
         stencil([&](int dx, int dy, int dz) {
