@@ -81,3 +81,72 @@ def test_configs_build():
     phi, cA, cB = fields()
     assert phi.shape == (1, 2, 32)
     assert float(cA[0, 0, 0]) == 0.55 and float(cB[0, 0, -1]) == 0.25
+
+
+def _brute_chi(a, walls):
+    """Euler characteristic by listing the cells of every closed unit cube (square) in doubled
+    coordinates: node p spans 2p..2p+2 along each axis, a coordinate is odd inside that span
+    and even on its boundary; a cell's dimension is its number of odd coordinates. Periodic
+    axes wrap modulo 2n. Each distinct cell counts (-1)^dimension."""
+    a = np.asarray(a) >= 0.5
+    walled = [walls[2], walls[1], walls[0]]
+    if a.shape[0] == 1:
+        a, walled = a[0], walled[1:]
+    cells = set()
+    for p in np.argwhere(a):
+        for off in np.ndindex(*([3] * a.ndim)):
+            c = []
+            for ax in range(a.ndim):
+                v = 2 * int(p[ax]) + off[ax]
+                if not walled[ax]:
+                    v %= 2 * a.shape[ax]
+                c.append(v)
+            cells.add(tuple(c))
+    return sum((-1) ** sum(v & 1 for v in c) for c in cells)
+
+
+def test_euler_closed_forms():
+    chi = measure.euler_characteristic
+    z = lambda: np.zeros((9, 10, 11))
+    a = z(); a[4, 5, 6] = 1
+    assert chi(a) == 1                                            # one closed cube: a ball
+    a = z(); a[2:5, 3:6, 4:7] = 1; a[3, 4, 5] = 0
+    assert chi(a) == 2                                            # a shell enclosing a cavity
+    a = z(); a[4, 3:6, 3:6] = 1; a[4, 4, 4] = 0
+    assert chi(a) == 0                                            # a ring: a solid torus
+    a = z(); a[1, 1, 1] = a[2, 2, 2] = 1
+    assert chi(a) == 1                                            # cubes sharing a corner: one region
+    a = z(); a[1, 1, 1] = a[3, 3, 3] = 1
+    assert chi(a) == 2
+    a = z(); a[4, 4, :] = 1
+    assert chi(a) == 0                                            # a rod closed on itself through x
+    assert chi(a, walls=(True, False, False)) == 1                # the same rod cut by x walls
+    assert chi(np.ones((5, 6, 7))) == 0                           # the 3-torus
+    assert chi(np.ones((5, 6, 7)), walls=(False, False, True)) == 0   # slab x 2-torus
+    assert chi(np.ones((5, 6, 7)), walls=(True, True, True)) == 1     # a box
+    a2 = np.zeros((1, 8, 9)); a2[0, 2:5, 2:5] = 1; a2[0, 3, 3] = 0
+    assert chi(a2) == 0                                           # 2D annulus
+    a2 = np.zeros((1, 8, 9)); a2[0, 2, 2] = a2[0, 3, 3] = 1
+    assert chi(a2) == 1                                           # 8-connected diagonal pair
+    assert chi(np.ones((1, 4, 5))) == 0 and chi(np.ones((1, 4, 5)), walls=(True, True, False)) == 1
+
+
+@pytest.mark.parametrize("walls", [(False, False, False), (True, False, False), (False, False, True),
+                                   (True, False, True)])
+@pytest.mark.parametrize("nz", [1, 5])
+def test_euler_matches_cell_enumeration_on_random_sets(walls, nz):
+    rng = np.random.default_rng(17 + nz)
+    for density in (0.1, 0.35, 0.6):
+        a = (rng.random((nz, 6, 7)) < density).astype(float)
+        w = walls if nz > 1 else (walls[0], walls[1], False)
+        assert measure.euler_characteristic(a, w) == _brute_chi(a, w)
+
+
+@pytest.mark.parametrize("walls", [(False, False, False), (False, False, True)])
+def test_euler_counts_droplets(walls):
+    shape = (40, 36, 44)
+    centres, radii = place_droplets(shape, 0.12, 3.0, 6.0, 3.0, seed=21, walls=walls)
+    phi = phi_field(shape, centres, radii, 3.0, walls=walls).numpy()
+    n = measure.count_droplets(phi, walls)
+    assert n == len(radii) > 10
+    assert measure.euler_characteristic(phi, walls) == n
