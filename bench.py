@@ -365,10 +365,12 @@ def gb300(args):
         v = Simulation(p3, *f3(device=device), device=device)
         vs = max(20, args.steps // 2)
         vms, _, _ = time_device(v, vs, args.warmup, dist)
+        s3 = v.sums()
         b3 = 2 * 21 * 4.0
         var["ripening_3d"] = {"value": ws * p3.nodes * vs / (vms / 1e3) / 1e6, "unit": "MLUPS",
                               "ms_per_step": vms / vs, "workload": "256^3 D3Q7, no flow, fraction 0.15, FP32, in place",
-                              "alg_bytes_per_node": b3, "roofline_frac": b3 * p3.nodes / (vms / vs / 1e3) / 1e9 / peak}
+                              "alg_bytes_per_node": b3, "roofline_frac": b3 * p3.nodes / (vms / vs / 1e3) / 1e9 / peak,
+                              "droplets_N": s3["euler"], "after_steps": args.warmup + vs}
         del v
         torch.cuda.synchronize()
         # 2D ripening without flow on D2Q9 (§4.2.2 table): 4096^2, 27 FP32 populations in place,
@@ -467,7 +469,8 @@ def drift_study(args):
             if t:
                 sim.step(every)
             s = sim.sums()
-            series.append({"t": t, "phi": s["phi"], "cA": s["cA"], "cB": s["cB"], "p": s["p"], "umax": s["umax"]})
+            series.append({"t": t, "phi": s["phi"], "cA": s["cA"], "cB": s["cB"], "p": s["p"], "umax": s["umax"],
+                           "N": s["euler"]})
         torch.cuda.synchronize()
         runs[storage] = {"series": series, "seconds": time.perf_counter() - t0}
         del sim
@@ -480,14 +483,16 @@ def drift_study(args):
         out["runs"][storage] = {
             "rel_drift_cA": (s1["cA"] - s0["cA"]) / s0["cA"], "rel_drift_cB": (s1["cB"] - s0["cB"]) / s0["cB"],
             "max_rel_dev_phi_vs_f32": max(abs(a["phi"] - b["phi"]) / abs(b["phi"]) for a, b in zip(r["series"], ref)),
-            "phi_change": (s1["phi"] - s0["phi"]) / s0["phi"], "umax_end": s1["umax"], "seconds": r["seconds"],
+            "phi_change": (s1["phi"] - s0["phi"]) / s0["phi"], "umax_end": s1["umax"],
+            "droplets_start": s0["N"], "droplets_end": s1["N"], "seconds": r["seconds"],
             "series": r["series"]}
     print(json.dumps(out))
 
 
 def ripening_law(args):
     """<R>^3 against t. 3D (256^3, D3Q7, FP32): the Sauter radius R = 3 V / A from the
-    volume V = sum phi and the interface area A = sum (4/W) phi (1 - phi); 2D (4096^2, D2Q9):
+    volume V = sum phi and the interface area A = sum (4/W) phi (1 - phi), beside the droplet
+    count N (Euler characteristic) and sqrt(A / (4 pi N)); 2D (4096^2, D2Q9):
     <R> = A / (2 pi N) of Eq. 67 with the droplet count N of the Euler characteristic. Least-
     squares line of <R>^3 over the second half of the run, with its R^2."""
     import torch
@@ -508,7 +513,8 @@ def ripening_law(args):
                 R = s["interface"] / (2 * math.pi * s["euler"]) if s["euler"] > 0 else float("nan")
                 series.append({"t": t, "R": R, "N": s["euler"]})
             else:
-                series.append({"t": t, "R": 3.0 * s["phi"] / s["interface"]})
+                R_n = math.sqrt(s["interface"] / (4 * math.pi * s["euler"])) if s["euler"] > 0 else float("nan")
+                series.append({"t": t, "R": 3.0 * s["phi"] / s["interface"], "N": s["euler"], "R_area_per_N": R_n})
         half = [e for e in series if e["t"] >= args.ripening_law / 2]
         ts = [e["t"] for e in half]
         ys = [e["R"] ** 3 for e in half]

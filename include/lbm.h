@@ -113,9 +113,13 @@ enum {
     LBM_RED_NONFINITE,   /* number of nodes with a non-finite moment */
     LBM_RED_INTERFACE,   /* sum (4/W) phi (1 - phi): interface length (2D) or area (3D); Eq. 67 gives
                           * the mean droplet radius <R> = this / (2 pi N) in 2D */
-    LBM_RED_EULER,       /* 2D lattices: Euler characteristic of {phi >= 1/2} with 8-connected
-                          * droplets (Gray's 2x2 bit quads, one pass), i.e. the droplet count N
-                          * when no droplet has a hole (§4.2.2 measures N this way); 0 in 3D */
+    LBM_RED_EULER,       /* Euler characteristic of {phi >= 1/2} taken as the union of closed
+                          * unit squares (2D: 8-connected droplets, Gray's 2x2 bit quads) or
+                          * cubes (3D: 26-connected, vertices - edges + faces - cubes of that
+                          * union, each node owning the cells at its low corner); outside an
+                          * x or z wall is empty. It is the droplet count N when no droplet
+                          * has a hole or a handle (§4.2.2 measures N this way). A 3D lattice
+                          * with nz == 1 and no z walls is a slab closed on itself: 0 */
     LBM_NRED
 };
 
@@ -125,7 +129,8 @@ typedef struct lbm_ctx lbm_ctx;
 size_t lbm_state_bytes(const lbm_params* p);
 
 /* Bytes of scratch the step needs beside the state: the phi field (read by the capillary
- * stencil with flow, and by the droplet count of lbm_reduce on the 2D lattices) and the
+ * stencil with flow, and by the droplet count of lbm_reduce on the 2D lattices), one bit
+ * per node of phi >= 1/2 (the droplet count of lbm_reduce on the 3D lattices) and the
  * block partials of lbm_reduce. */
 size_t lbm_work_bytes(const lbm_params* p);
 
@@ -243,11 +248,12 @@ lbm_status lbm_adjoint_theta(const lbm_params* p, void* d_adj_work, double* out,
  * application that hands this library its state buffer but owns every allocation, or a
  * real-time loop where allocation is forbidden after start-up). Same results as
  * lbm_reduce for the state copy d_state holds at time t (the buffer lbm_init was given),
- * but the reduction's scratch (block partials, results, and for flow or 2D lattices the phi
- * field) lives
+ * but the reduction's scratch (block partials, results, for flow or 2D lattices the phi
+ * field, for 3D lattices one bit per node) lives
  * in a file-scope device array of 4 MiB that every GPU loading this library holds until
  * the process exits. Lattices whose scratch exceeds 4 MiB (flow or 2D lattices above about
- * one million nodes) are rejected with LBM_ERR_ARG. The call allocates nothing. The first call
+ * one million nodes, 3D lattices without flow above about 33 million) are rejected with
+ * LBM_ERR_ARG. The call allocates nothing. The first call
  * on each device looks up the array's device address (cudaGetSymbolAddress) with that
  * device current; make that first call before any stream capture. Every call shares the
  * array and leaves its contents behind; the kernels overwrite all of it that they read, so

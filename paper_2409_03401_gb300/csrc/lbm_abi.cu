@@ -36,7 +36,7 @@ struct Layout {
     size_t copy = 0;           // bytes of one copy
     size_t state = 0, work = 0;
     size_t off_f = 0, off_g = 0, off_hA = 0, off_hB = 0, off_rest = 0;
-    size_t off_phi = 0, off_partials = 0, off_out = 0;
+    size_t off_phi = 0, off_bits = 0, off_partials = 0, off_out = 0;
 };
 
 const char* check_params(const lbm_params* p) {
@@ -86,6 +86,8 @@ Layout layout_of(const lbm_params* p) {
     size_t w = 0;
     // the phi field: read by the capillary stencil (flow) and by the 2D Euler count
     L.off_phi = w;      w += (p->flow || two_d(p->lattice)) ? round_up((size_t)L.plane * real, kAlign) : 0;
+    // one bit per node of phi >= 1/2: the 3D Euler count
+    L.off_bits = w;     w += two_d(p->lattice) ? 0 : round_up((size_t)((L.n + 31) / 32) * sizeof(unsigned), kAlign);
     L.off_partials = w; w += round_up((size_t)kRedBlocks * LBM_NRED * sizeof(double), kAlign);
     L.off_out = w;      w += round_up(LBM_NRED * sizeof(double), kAlign);
     L.work = w;
@@ -439,7 +441,7 @@ lbm_status lbm_reduce(lbm_ctx* c, double* out) {
     double* partials = reinterpret_cast<double*>(c->work + c->L.off_partials);
     double* dout = reinterpret_cast<double*>(c->work + c->L.off_out);
     LBM_DISPATCH(c->p.storage, launch_reduce, c->dp, current(c), c->p.lattice, c->p.flow != 0, read_mode(c),
-                 c->work + c->L.off_phi, partials, kRedBlocks, c->stream);
+                 c->work + c->L.off_phi, c->work + c->L.off_bits, partials, kRedBlocks, c->stream);
     reduce_final<<<1, 256, 0, c->stream>>>(partials, kRedBlocks, dout);
     lbm_status s = cuda_check(c, "reduce kernel launch");
     if (s != LBM_OK) return s;
@@ -645,7 +647,7 @@ extern "C" lbm_status lbm_reduce_static(const lbm_params* p, const void* d_state
     if (L.work > kStaticScratchBytes)
         return fail(nullptr, LBM_ERR_ARG,
                     "lbm_reduce_static: this lattice needs " + std::to_string(L.work) +
-                        " bytes of scratch (the phi field of a flow lattice) but the static array holds " +
+                        " bytes of scratch (phi field, bit field and partials) but the static array holds " +
                         std::to_string(kStaticScratchBytes) + "; use lbm_reduce with a work buffer");
     void* scratch = nullptr;
     lbm_status s = static_scratch(&scratch);
@@ -659,8 +661,8 @@ extern "C" lbm_status lbm_reduce_static(const lbm_params* p, const void* d_state
     double* dout = reinterpret_cast<double*>(w + L.off_out);
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     cudaGetLastError();
-    LBM_DISPATCH(p->storage, launch_reduce, dp, st, p->lattice, p->flow != 0, mode, w + L.off_phi, partials,
-                 kRedBlocks, cs);
+    LBM_DISPATCH(p->storage, launch_reduce, dp, st, p->lattice, p->flow != 0, mode, w + L.off_phi,
+                 w + L.off_bits, partials, kRedBlocks, cs);
     reduce_final<<<1, 256, 0, cs>>>(partials, kRedBlocks, dout);
     s = cuda_check(nullptr, "static reduce launch");
     if (s != LBM_OK) return s;

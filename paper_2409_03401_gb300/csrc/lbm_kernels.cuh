@@ -828,51 +828,129 @@ __device__ __forceinline__ double euler_quads(const R* __restrict__ phi, int x, 
     return 0.25 * q;
 }
 
-// FP64 block partials of the global diagnostics (grid-stride over nodes).
-template <class T, int LAT, bool FLOW, int MODE>
-__global__ void __launch_bounds__(256)
-reduce_kernel(const DevParams P, const StateView st, const typename RealOf<T>::type* __restrict__ phi_field,
-              double* __restrict__ partials) {
-    using R = typename RealOf<T>::type;
-    double acc[LBM_NRED_DEV];
+// Euler characteristic of the 26-connected set {phi >= 1/2} of a 3D lattice: the alternating
+// count of the vertices, edges, faces and cubes of the union of closed unit cubes centred on
+// the set nodes. Position (x, y, z) owns the cube of node (x, y, z), the faces on its low
+// x, y and z sides, the edges along x, y and z through the corner line on its low sides, and
+// its low corner vertex (x - 1/2, y - 1/2, z - 1/2); a cell belongs to the union when any
+// node it bounds is set (b[c][b][a]: node (x - 1 + a, y - 1 + b, z - 1 + c)). Outside an x
+// or z wall is empty; other axes wrap. bits: bit (id & 31) of word id >> 5 is node id's
+// phi >= 1/2, ids x fastest.
+__device__ __forceinline__ int euler_cells(const unsigned* __restrict__ bits, int x, int y, int z,
+                                           const DevParams& P) {
+    int b[2][2][2];
 #pragma unroll
-    for (int i = 0; i < LBM_NRED_DEV; ++i) acc[i] = 0.0;
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                int xx = x - 1 + a, yy = y - 1 + bb, zz = z - 1 + c;
+                bool inside = true;
+                if (xx < 0) { inside = !P.wall_x; xx += P.nx; }
+                if (xx >= P.nx) { inside = !P.wall_x; xx -= P.nx; }
+                if (yy < 0) yy += P.ny;
+                if (zz < 0) { inside = inside && !P.wall_z; zz += P.nz; }
+                if (zz >= P.nz) { inside = inside && !P.wall_z; zz -= P.nz; }
+                const long long id = ((long long)zz * P.ny + yy) * P.nx + xx;
+                b[c][bb][a] = inside ? int((__ldg(bits + (id >> 5)) >> (id & 31)) & 1u) : 0;
+            }
+    const int vert = b[0][0][0] | b[0][0][1] | b[0][1][0] | b[0][1][1] | b[1][0][0] | b[1][0][1] | b[1][1][0] |
+                     b[1][1][1];
+    const int ex = b[0][0][1] | b[0][1][1] | b[1][0][1] | b[1][1][1];
+    const int ey = b[0][1][0] | b[0][1][1] | b[1][1][0] | b[1][1][1];
+    const int ez = b[1][0][0] | b[1][0][1] | b[1][1][0] | b[1][1][1];
+    const int fx = b[1][1][0] | b[1][1][1];
+    const int fy = b[1][0][1] | b[1][1][1];
+    const int fz = b[0][1][1] | b[1][1][1];
+    return vert - (ex + ey + ez) + (fx + fy + fz) - b[1][1][1];
+}
+
+// Writes slot LBM_RED_EULER of every block's partials (the reduction kernel leaves it 0 on
+// 3D lattices). Along a walled axis the cell positions run one past the last node: that
+// node owns the positions on the wall too.
+template <class T>
+__global__ void __launch_bounds__(256)
+euler3d_kernel(const DevParams P, const unsigned* __restrict__ bits, double* __restrict__ partials) {
+    long long acc = 0;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < P.n; id += stride) {
         const int x = int(id % P.nx);
         const int y = int((id / P.nx) % P.ny);
         const int z = int(id / ((long long)P.nx * P.ny));
-        Addr<MODE> ad;
-        ad.self = int(id);
-        ad.nb.init(x, y, z, P);
-        Node<T, LAT, FLOW> nd;
-        nd.gather(st, ad, P);
-        nd.moments(P);
-        R phi;
-        if constexpr (FLOW) phi = phi_field[id]; else phi = nd.phi();
-        double umag = 0.0, ph = 0.0;
-        if constexpr (FLOW) {
-            R gx, gy, gz, lap, Fx, Fy, Fz, ux, uy, uz;
-            stencil([&](int dx, int dy, int dz) { return ad.phi(phi_field, dx, dy, dz); }, phi, gx, gy, gz, lap);
-            force_velocity(nd, phi, gx, gy, gz, lap, P, Fx, Fy, Fz, ux, uy, uz);
-            umag = sqrt(double(ux) * ux + double(uy) * uy + double(uz) * uz);
-            ph = nd.flow_p();
-        }
-        const double vals[5] = {double(phi), double(nd.dcA) + P.c0[0], double(nd.dcB) + P.c0[1], ph,
-                                double(nd.S)};
-        bool finite = true;
+        const int x1 = (P.wall_x && x == P.nx - 1) ? P.nx : x;
+        const int z1 = (P.wall_z && z == P.nz - 1) ? P.nz : z;
+        for (int zs = z; zs <= z1; ++zs)
+            for (int xs = x; xs <= x1; ++xs) acc += euler_cells(bits, xs, y, zs, P);
+    }
+    __shared__ long long sm[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) sm[warp] = acc;
+    __syncthreads();
+    if (warp == 0) {
+        long long v = lane < int(blockDim.x >> 5) ? sm[lane] : 0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) partials[(long long)blockIdx.x * LBM_NRED_DEV + (LBM_NRED_DEV - 1)] = double(v);
+    }
+}
+
+// FP64 block partials of the global diagnostics (grid-stride over nodes; the 32 nodes a warp
+// visits together are consecutive and start at a multiple of 32). On 3D lattices it also
+// writes the bit field of phi >= 1/2 that euler3d_kernel reads, one warp vote per word.
+template <class T, int LAT, bool FLOW, int MODE>
+__global__ void __launch_bounds__(256)
+reduce_kernel(const DevParams P, const StateView st, const typename RealOf<T>::type* __restrict__ phi_field,
+              unsigned* __restrict__ bits, double* __restrict__ partials) {
+    using R = typename RealOf<T>::type;
+    double acc[LBM_NRED_DEV];
 #pragma unroll
-        for (int i = 0; i < 5; ++i) { acc[i] += vals[i]; finite = finite && isfinite(vals[i]); }
-        finite = finite && isfinite(umag) && isfinite(double(nd.phit));
-        acc[5] = fmax(acc[5], isfinite(umag) ? umag : 0.0);
-        acc[6] += double(nd.phit);
-        acc[7] += finite ? 0.0 : 1.0;
-        acc[8] += 4.0 / P.W * double(phi) * (1.0 - double(phi));          // Eq. 67 integrand
-        if constexpr (kTwoD<LAT>) acc[9] += euler_quads(phi_field, x, y, P);
+    for (int i = 0; i < LBM_NRED_DEV; ++i) acc[i] = 0.0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < P.n; base += stride) {
+        const long long id = base + lane;
+        bool on = false;
+        if (id < P.n) {
+            const int x = int(id % P.nx);
+            const int y = int((id / P.nx) % P.ny);
+            const int z = int(id / ((long long)P.nx * P.ny));
+            Addr<MODE> ad;
+            ad.self = int(id);
+            ad.nb.init(x, y, z, P);
+            Node<T, LAT, FLOW> nd;
+            nd.gather(st, ad, P);
+            nd.moments(P);
+            R phi;
+            if constexpr (FLOW) phi = phi_field[id]; else phi = nd.phi();
+            double umag = 0.0, ph = 0.0;
+            if constexpr (FLOW) {
+                R gx, gy, gz, lap, Fx, Fy, Fz, ux, uy, uz;
+                stencil([&](int dx, int dy, int dz) { return ad.phi(phi_field, dx, dy, dz); }, phi, gx, gy, gz, lap);
+                force_velocity(nd, phi, gx, gy, gz, lap, P, Fx, Fy, Fz, ux, uy, uz);
+                umag = sqrt(double(ux) * ux + double(uy) * uy + double(uz) * uz);
+                ph = nd.flow_p();
+            }
+            const double vals[5] = {double(phi), double(nd.dcA) + P.c0[0], double(nd.dcB) + P.c0[1], ph,
+                                    double(nd.S)};
+            bool finite = true;
+#pragma unroll
+            for (int i = 0; i < 5; ++i) { acc[i] += vals[i]; finite = finite && isfinite(vals[i]); }
+            finite = finite && isfinite(umag) && isfinite(double(nd.phit));
+            acc[5] = fmax(acc[5], isfinite(umag) ? umag : 0.0);
+            acc[6] += double(nd.phit);
+            acc[7] += finite ? 0.0 : 1.0;
+            acc[8] += 4.0 / P.W * double(phi) * (1.0 - double(phi));          // Eq. 67 integrand
+            if constexpr (kTwoD<LAT>) acc[9] += euler_quads(phi_field, x, y, P);
+            on = phi >= R(0.5);
+        }
+        if constexpr (!kTwoD<LAT>) {
+            const unsigned word = __ballot_sync(0xffffffffu, on);
+            if (lane == 0) bits[base >> 5] = word;
+        }
     }
     // block reduction: warp shuffles, then one warp over the warp results
     __shared__ double sm[LBM_NRED_DEV][32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < LBM_NRED_DEV; ++i) {
         double v = acc[i];
@@ -984,14 +1062,16 @@ struct Launchers {
         LBM_MODE_SWITCH(mode, fields_kernel<T, LAT, FLOW, M><<<grid, bx, 0, s>>>(P, st, phi, out));
     }
     template <int LAT, bool FLOW>
-    static void reduce(const DevParams& P, const StateView& st, int mode, void* phi_work, double* partials,
-                       int nblocks, cudaStream_t s) {
+    static void reduce(const DevParams& P, const StateView& st, int mode, void* phi_work, void* bits_work,
+                       double* partials, int nblocks, cudaStream_t s) {
         R* phi = static_cast<R*>(phi_work);
+        unsigned* bits = static_cast<unsigned*>(bits_work);
         if constexpr (FLOW || kTwoD<LAT>) {
             int bx; const dim3 grid = node_grid(P, bx);
             LBM_MODE_SWITCH(mode, phi_kernel<T, LAT, M><<<grid, bx, 0, s>>>(P, st, phi));
         }
-        LBM_MODE_SWITCH(mode, reduce_kernel<T, LAT, FLOW, M><<<nblocks, 256, 0, s>>>(P, st, phi, partials));
+        LBM_MODE_SWITCH(mode, reduce_kernel<T, LAT, FLOW, M><<<nblocks, 256, 0, s>>>(P, st, phi, bits, partials));
+        if constexpr (!kTwoD<LAT>) euler3d_kernel<T><<<nblocks, 256, 0, s>>>(P, bits, partials);
     }
 };
 
@@ -1036,15 +1116,16 @@ struct Launchers {
         else Launchers<T>::fields<LAT_D3Q7, false>(P, st, mode, phi, out, s);                              \
     }                                                                                                     \
     void launch_reduce_##SUFFIX(const DevParams& P, const StateView& st, int lat, bool flow, int mode,    \
-                                void* phi, double* partials, int nblocks, cudaStream_t s) {               \
-        if (lat == LAT_D2Q5) Launchers<T>::reduce<LAT_D2Q5, false>(P, st, mode, phi, partials, nblocks, s); \
-        else if (lat == LAT_D2Q9) Launchers<T>::reduce<LAT_D2Q9, false>(P, st, mode, phi, partials, nblocks, s); \
+                                void* phi, void* bits, double* partials, int nblocks, cudaStream_t s) {   \
+        if (lat == LAT_D2Q5) Launchers<T>::reduce<LAT_D2Q5, false>(P, st, mode, phi, bits, partials, nblocks, s); \
+        else if (lat == LAT_D2Q9)                                                                         \
+            Launchers<T>::reduce<LAT_D2Q9, false>(P, st, mode, phi, bits, partials, nblocks, s);           \
         else if (lat == LAT_D3Q19 && flow)                                                                \
-            Launchers<T>::reduce<LAT_D3Q19, true>(P, st, mode, phi, partials, nblocks, s);                 \
+            Launchers<T>::reduce<LAT_D3Q19, true>(P, st, mode, phi, bits, partials, nblocks, s);           \
         else if (lat == LAT_D3Q19)                                                                        \
-            Launchers<T>::reduce<LAT_D3Q19, false>(P, st, mode, phi, partials, nblocks, s);                \
-        else if (flow) Launchers<T>::reduce<LAT_D3Q7, true>(P, st, mode, phi, partials, nblocks, s);       \
-        else Launchers<T>::reduce<LAT_D3Q7, false>(P, st, mode, phi, partials, nblocks, s);                \
+            Launchers<T>::reduce<LAT_D3Q19, false>(P, st, mode, phi, bits, partials, nblocks, s);          \
+        else if (flow) Launchers<T>::reduce<LAT_D3Q7, true>(P, st, mode, phi, bits, partials, nblocks, s); \
+        else Launchers<T>::reduce<LAT_D3Q7, false>(P, st, mode, phi, bits, partials, nblocks, s);          \
     }
 
 }  // namespace lbm

@@ -28,7 +28,7 @@ constexpr int kModeAAEven = 0, kModeAAOdd = 1, kModePull = 2;
     void launch_fields_##SUFFIX(const DevParams&, const StateView&, int lat, bool flow, int mode,        \
                                 void* phi, FieldPtrs, cudaStream_t);                                     \
     void launch_reduce_##SUFFIX(const DevParams&, const StateView&, int lat, bool flow, int mode,        \
-                                void* phi, double* partials, int nblocks, cudaStream_t);
+                                void* phi, void* bits, double* partials, int nblocks, cudaStream_t);
 
 void launch_adjoint_step(const DevParams&, const StateView&, int storage, int lat, bool odd, const void* lam_next,
                          void* lam, double* partials, cudaStream_t);

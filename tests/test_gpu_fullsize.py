@@ -85,3 +85,13 @@ def test_full_lattice_invariants(full_run):
     assert float(phi.min()) > -0.05 and float(phi.max()) < 1.05
     # initial sums against the FP64 inputs
     assert abs(s0["cA"] - float(init[1].sum())) <= 1e-6 * float(init[1].sum())
+
+
+def test_full_lattice_droplet_count(full_run):
+    # the Euler count of the reduction on the whole 512^3 lattice: the placed droplets at
+    # t = 0 (none overlap or touch a wall), and the oracle's count of the GPU's phi after the steps
+    from oracle import measure
+    p, _, out, s0, s1, geometry = full_run
+    assert s0["euler"] == float(len(geometry[1]))
+    phi = out["phi"].cpu().numpy()
+    assert s1["euler"] == float(measure.euler_characteristic(phi, (p.wall_x, False, p.wall_z)))

@@ -73,13 +73,6 @@ def test_droplet_count_and_mean_radius(walls):
     assert abs(R_gpu - R_ref) <= 1e-5 * R_ref
 
 
-def test_euler_is_zero_on_3d_lattices():
-    p, fields = configs.ripening(shape=(12, 14, 16))
-    sim, _ = run_gpu(p, fields(), 2)
-    s = sim.sums()
-    assert s["euler"] == 0.0 and s["interface"] > 0
-
-
 def test_full_size_4096_squared_matches_oracle():
     # the 4096^2 D2Q9 run as the bench times it (FP32, in place), against the oracle on the
     # whole lattice after 3 steps, and the droplet count of the initial field
