@@ -65,18 +65,19 @@ def _droplet_workload(p, fraction, r_min, r_max, seed, sample_volume=False, supe
     return fields
 
 
-def ripening(n=256, storage="f32", shape=None, seed=2):
+def ripening(n=256, storage="f32", shape=None, seed=2, supersaturation=SUPERSATURATION):
     """3D Ostwald ripening without flow, periodic, spheres at fraction 0.15, r in [4, 10]."""
     nz, ny, nx = shape or (n, n, n)
     p = LBMParams(nx=nx, ny=ny, nz=nz, lattice="D3Q7", flow=False, storage=storage)
-    return p, _droplet_workload(p, 0.15, 4.0, 10.0, seed)
+    return p, _droplet_workload(p, 0.15, 4.0, 10.0, seed, supersaturation=supersaturation)
 
 
-def sedimentation(n=512, storage="f32", shape=None, seed=3, fraction=0.2, r=(6.0, 16.0)):
+def sedimentation(n=512, storage="f32", shape=None, seed=3, fraction=0.2, r=(6.0, 16.0),
+                  supersaturation=SUPERSATURATION):
     """3D coarsening with flow and buoyancy, walls at the z ends."""
     nz, ny, nx = shape or (n, n, n)
     p = LBMParams(nx=nx, ny=ny, nz=nz, lattice="D3Q7", flow=True, storage=storage, wall_z=True)
-    return p, _droplet_workload(p, fraction, r[0], r[1], seed)
+    return p, _droplet_workload(p, fraction, r[0], r[1], seed, supersaturation=supersaturation)
 
 
 # 2D ripening without flow (§4.2.2 table, D2Q9): the table's collision times tau_g = 0.8776,
