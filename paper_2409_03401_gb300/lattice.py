@@ -28,6 +28,11 @@ class Simulation:
         device = torch.device(device)
         if device.type != "cuda":
             raise ValueError("Simulation needs a CUDA device")
+        # the library reads nx*ny*nz values of each initial field: check before any device call
+        n = params.nx * params.ny * params.nz
+        for name, t in (("phi0", phi0), ("cA0", cA0), ("cB0", cB0)):
+            if t.numel() != n:
+                raise ValueError(f"{name} has {t.numel()} values; the lattice has nx*ny*nz = {n}")
         self.lib = _lib.load()
         self.params = params
         self.device = device
@@ -49,14 +54,29 @@ class Simulation:
 
     @classmethod
     def attach(cls, params, state, t, device=None, stream=None):
-        """Resume from a state tensor saved earlier (checkpoint/resume)."""
+        """Resume from a state tensor saved earlier (checkpoint/resume). ``state``: a
+        contiguous uint8 CUDA tensor holding at least lbm_state_bytes(params) bytes, as
+        written by the same build of the library for the same parameters."""
         self = cls.__new__(cls)
-        device = torch.device(device or state.device)
         self.lib = _lib.load()
+        self._cp = _lib.make_params(params)
+        need = self.lib.lbm_state_bytes(ctypes.byref(self._cp))
+        if need == 0:
+            raise _lib.LBMError(_lib.LBM_ERR_ARG, "invalid parameters")
+        # the library cannot see the buffer's size: a short one would be read out of bounds
+        if state.dtype != torch.uint8 or not state.is_contiguous() or state.numel() < need:
+            raise ValueError(f"state must be a contiguous uint8 tensor of at least {need} bytes "
+                             f"(got {state.dtype}, {state.numel()} elements)")
+        if state.device.type != "cuda":
+            raise ValueError("state must live on a CUDA device")
+        if device is not None:
+            want = torch.device(device)
+            if want.type != "cuda" or (want.index is not None and want != state.device):
+                raise ValueError(f"state is on {state.device}, not on {want}")
+        device = state.device
         self.params = params
         self.device = device
         self.stream = stream or torch.cuda.current_stream(device)
-        self._cp = _lib.make_params(params)
         wbytes = self.lib.lbm_work_bytes(ctypes.byref(self._cp))
         self.state = state
         self.work = torch.empty(wbytes, dtype=torch.uint8, device=device)
@@ -102,6 +122,9 @@ class Simulation:
 
     def fields(self, names=_lib.FIELDS):
         """Dict of (nz, ny, nx) tensors of the current time level."""
+        unknown = [k for k in names if k not in _lib.FIELDS]
+        if unknown:
+            raise ValueError(f"unknown fields {unknown}; the library writes {_lib.FIELDS}")
         out = {k: torch.empty(self.params.shape, dtype=self.real_dtype, device=self.device) for k in names}
         ptrs = (ctypes.c_void_p * _lib.NFIELDS)()
         for i, k in enumerate(_lib.FIELDS):

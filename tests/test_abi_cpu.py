@@ -93,3 +93,26 @@ def test_header_is_plain_c99(tmp_path):
                           "-I", cuda_inc, "-c", os.path.join(ROOT, "tests", "c_abi_example.c"),
                           "-o", str(tmp_path / "c_abi_example.o")], capture_output=True, text=True)
     assert out.returncode == 0, out.stderr
+
+
+def test_python_binding_checks_buffers_before_any_device_call(lib):
+    # wrong-sized inputs would be read out of bounds by the kernels: the binding refuses them
+    import torch
+    from paper_2409_03401_gb300 import Simulation
+    from workloads import configs
+    p, fields = configs.ripening(shape=(8, 9, 10))
+    phi, cA, cB = fields()
+    with pytest.raises(ValueError, match="phi0 has"):
+        Simulation(p, phi[:4], cA, cB, device="cuda:0")
+    with pytest.raises(ValueError, match="cB0 has"):
+        Simulation(p, phi, cA, cB.reshape(-1)[:-1], device="cuda:0")
+    with pytest.raises(ValueError, match="CUDA device"):
+        Simulation(p, phi, cA, cB, device="cpu")
+    from paper_2409_03401_gb300 import _lib
+    need = lib.lbm_state_bytes(ctypes.byref(_lib.make_params(p)))
+    with pytest.raises(ValueError, match="at least"):
+        Simulation.attach(p, torch.empty(need - 1, dtype=torch.uint8), 0)
+    with pytest.raises(ValueError, match="at least"):
+        Simulation.attach(p, torch.empty(need // 4, dtype=torch.float32), 0)
+    with pytest.raises(ValueError, match="CUDA device"):
+        Simulation.attach(p, torch.empty(need, dtype=torch.uint8), 0)
