@@ -31,6 +31,11 @@ class CoupledRun(torch.autograd.Function):
     def forward(ctx, phi0, theta, params, cA0, cB0, steps, K):
         if params.flow:
             raise ValueError("the adjoint covers the step without flow")
+        if params.storage not in ("f32", "f64"):
+            raise ValueError("the adjoint needs f32 or f64 storage")
+        if int(K) < 1 or int(steps) < 0:
+            raise ValueError(f"need K >= 1 and steps >= 0 (got K = {K}, steps = {steps})")
+        steps, K = int(steps), int(K)
         p = _with_theta(params, theta.detach().cpu())
         device = phi0.device
         phi0d = phi0.detach().to(device=device, dtype=torch.float64).contiguous()

@@ -116,3 +116,21 @@ def test_python_binding_checks_buffers_before_any_device_call(lib):
         Simulation.attach(p, torch.empty(need // 4, dtype=torch.float32), 0)
     with pytest.raises(ValueError, match="CUDA device"):
         Simulation.attach(p, torch.empty(need, dtype=torch.uint8), 0)
+
+
+def test_adjoint_wrapper_rejects_bad_arguments_up_front(lib):
+    # checked before the forward run: K = 0 would never advance the checkpoint loop
+    import torch
+    from paper_2409_03401_gb300.adjoint import CoupledRun
+    from workloads import configs
+    p, fields = configs.ripening(shape=(8, 9, 10))
+    phi, cA, cB = fields()
+    th = torch.tensor([0.1, 0.1, 0.1], dtype=torch.float64)
+    with pytest.raises(ValueError, match="K >= 1"):
+        CoupledRun.apply(phi, th, p, cA, cB, 10, 0)
+    with pytest.raises(ValueError, match="steps >= 0"):
+        CoupledRun.apply(phi, th, p, cA, cB, -1, 5)
+    with pytest.raises(ValueError, match="f32 or f64"):
+        CoupledRun.apply(phi, th, p.with_(storage="f16"), cA, cB, 10, 5)
+    with pytest.raises(ValueError, match="without flow"):
+        CoupledRun.apply(phi, th, p.with_(flow=True), cA, cB, 10, 5)
