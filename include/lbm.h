@@ -3,11 +3,12 @@
  *
  * The method (Verdier, Cartalade, Plapp, "Grand-potential phase field simulations
  * of droplet growth and sedimentation in a two-phase ternary fluid") couples, on
- * one lattice, four BGK lattice Boltzmann equations:
+ * one lattice, four lattice Boltzmann equations:
  *   g     - the Allen-Cahn phase field phi with its source S_phi   (§3.2, Eqs. 46-49, 35)
  *   h^A,B - the compositions c^A, c^B; mu from the closure Eq. 33  (§3.3, Eqs. 50-52)
  *   f     - incompressible flow with capillary + buoyancy forcing  (§3.1, Eqs. 36-45, 34)
- * g, h^A, h^B use D2Q5 (2D) or D3Q7 (3D); f uses the D3Q19 set of the paper's table.
+ * g, h^A, h^B use D2Q5 or D2Q9 (2D), D3Q7 or D3Q19 (3D) with BGK collisions; f uses
+ * D3Q19 with a BGK, TRT or MRT collision.
  * One call of lbm_step advances every population set by one fused collide-and-stream
  * pass over HBM: in-place AA-pattern streaming without flow; with flow, by default, a
  * two-buffer pull step that computes the capillary stencil's phi on the fly.
@@ -57,7 +58,6 @@ typedef enum { LBM_D2Q5 = 0, LBM_D3Q7 = 1, LBM_D3Q19 = 2, LBM_D2Q9 = 3 } lbm_lat
  * mu (Eq. 33) does not inherit the rounding of c itself. */
 typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16 = 2, LBM_BF16 = 3 } lbm_storage;
 
-/* Model parameters in lattice units (dx = dt = 1, rho_0 = 1), named as in the paper. */
 /* Flow collision operators. LBM_BGK is the paper's single-rate operator (Eq. 36). LBM_TRT and
  * LBM_MRT are the two- and multiple-relaxation-time operators the paper names as
  * alternatives (§3). TRT: the parts of f - f^eq even and odd under k -> opp(k) relax at
@@ -66,8 +66,9 @@ typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16 = 2, LBM_BF16 = 3 } lbm_storage
  * of Eq. 39 and F_k is added as in Eq. 36. */
 typedef enum { LBM_BGK = 0, LBM_TRT = 1, LBM_MRT = 2 } lbm_collision;
 
+/* Model parameters in lattice units (dx = dt = 1, rho_0 = 1), named as in the paper. */
 typedef struct lbm_params {
-    int32_t nx, ny, nz;      /* lattice extents; nz = 1 with LBM_D2Q5 */
+    int32_t nx, ny, nz;      /* lattice extents; nz = 1 with the 2D lattices (LBM_D2Q5, LBM_D2Q9) */
     int32_t lattice;         /* lbm_lattice of g, h^A, h^B */
     int32_t flow;            /* 1: D3Q19 flow populations, capillary (Eq. 34) + buoyancy forcing */
     int32_t storage;         /* lbm_storage */
@@ -87,7 +88,7 @@ typedef struct lbm_params {
     double sigma;            /* surface tension in Eq. 34 */
     double g[3];             /* buoyancy per unit phi: F_g = phi * g (§2.5, Delta rho g / rho_0) */
     double f_scale;          /* 16-bit storage scale of f_k / w_k: 0 or 1024 (fixed at 1024) */
-    int32_t collision;       /* flow collision, lbm_collision: LBM_BGK (Eq. 36) or LBM_TRT */
+    int32_t collision;       /* flow collision, lbm_collision: LBM_BGK (Eq. 36), LBM_TRT or LBM_MRT */
     double trt_magic;        /* LBM_TRT: Lambda = (1/omega+ - 1/2)(1/omega- - 1/2) > 0, where omega+
                               * is the BGK rate of Eq. 36 (it sets nu); 0 selects 3/16 */
     double mrt_rates[5];     /* LBM_MRT: rates in (0, 2) of the energy, energy-square, energy-flux,
@@ -151,11 +152,11 @@ lbm_status lbm_init(const lbm_params* p, void* d_state, void* d_work,
 lbm_status lbm_attach(const lbm_params* p, void* d_state, void* d_work, int64_t t,
                       void* stream, lbm_ctx** out);
 
-/* Advance nsteps >= 0 coupled time steps (§3, one fused collide-and-stream kernel
- * per step, plus the phi pass of the capillary stencil with flow). Asynchronous. */
+/* Advance nsteps >= 0 coupled time steps (§3): one fused collide-and-stream kernel per
+ * step; with flow, the in-place layout and the LBM_D3Q19 scalar lattice add a phi pass for
+ * the capillary stencil (lbm_kernels_per_step). Asynchronous. */
 lbm_status lbm_step(lbm_ctx* ctx, int nsteps);
 
-/* Current time level (number of steps since lbm_init). */
 /* Advance nsteps coupled time steps by replaying a CUDA graph of two steps (captured on the
  * first call from an even time level, after one plain pair of steps; kept until
  * lbm_destroy): the same kernels and results as lbm_step, bit for bit, with one launch per
@@ -165,6 +166,7 @@ lbm_status lbm_step(lbm_ctx* ctx, int nsteps);
  * this way are not recorded by lbm_profile_begin. No counterpart in the paper. */
 lbm_status lbm_step_graph(lbm_ctx* ctx, int nsteps);
 
+/* Current time level (number of steps since lbm_init, or t of lbm_attach); -1 for NULL. */
 int64_t lbm_time(const lbm_ctx* ctx);
 
 /* Macroscopic fields of the current time level into caller device buffers:
@@ -186,7 +188,8 @@ lbm_status lbm_reduce(lbm_ctx* ctx, double* out);
 lbm_status lbm_profile_begin(lbm_ctx* ctx, int max_steps);
 lbm_status lbm_profile_end(lbm_ctx* ctx, double* out);
 
-/* Number of kernels one lbm_step(ctx, 1) launches (2 for in-place flow, else 1). */
+/* Number of kernels one lbm_step(ctx, 1) launches: 2 with flow unless the state has two
+ * copies and the scalar lattice is LBM_D3Q7 (the fused kernel), else 1; 0 for NULL. */
 int lbm_kernels_per_step(const lbm_ctx* ctx);
 
 /* One step out of place, without a context: d_src holds one state copy at time t (the
