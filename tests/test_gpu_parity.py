@@ -186,6 +186,16 @@ def test_d3q19_scalar_lattice(storage, flow, inplace):
     _close(compare(q, fields(), 16), TOL[storage])
 
 
+# the D3Q19 scalar lattice with the TRT and MRT flow collisions: the per-node step's own
+# instances (MRT in a separate one), two copies (phi pass + pull step) and in place
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("collision,inplace", [("TRT", False), ("MRT", False), ("MRT", True)])
+def test_d3q19_scalar_lattice_trt_mrt(storage, collision, inplace):
+    p, fields = configs.sedimentation(shape=(14, 18, 70), fraction=0.05, r=(3.0, 5.0), storage=storage)
+    q = p.with_(lattice="D3Q19", collision=collision, nu=0.05, inplace=inplace)
+    _close(compare(q, fields(), 12), TOL[storage])
+
+
 def test_d3q19_scalar_lattice_fp16():
     p, fields = configs.sedimentation(shape=(24, 24, 40), fraction=0.06, r=(4.0, 6.0), storage="f16")
     errs = compare(p.with_(lattice="D3Q19"), fields(), 100)
