@@ -139,6 +139,19 @@ def test_lambda_star_reproduces_paper():
     assert abs(m.kinetic_coefficient(1.2e-3, got, 1.2, ce, (1.0, 0.8))) < 1e-15
 
 
+def test_closure_reproduces_the_couple_table_caption():
+    # §4.1 caption: the far-field compositions (0.4, 0.175) and (0.225, 0.6) are the chemical
+    # potentials (0.1, -0.125) in phase 0 and (-0.175, 0.2) in phase 1 (Eq. 33 with p(0) = 0,
+    # p(1) = 1 and the table's c_eq = (0.3, 0.3), (0.4, 0.4))
+    ce = ((0.3, 0.3), (0.4, 0.4))
+    for side, phi in (("minus", 0.0), ("plus", 1.0)):
+        for a, comp in enumerate("AB"):
+            c = PV[f"couple_c_{side}_{comp}"][0]
+            want = PV[f"couple_mu_{side}_{comp}"][0]
+            got = m.mu_closure(c, phi, ce[0][a], ce[1][a])
+            assert abs(got - want) < 1e-15, (side, comp, got, want)
+
+
 def test_relaxation_time_mapping_matches_2d_table():
     # §4.2.3 table: classic tau = 1/rate for M_phi = 1.2, M^A = 1, M^B = 0.8 with the
     # table's dx, dt on D2Q9 (c_s^2 = 1/3): lattice D = M dt / dx^2
