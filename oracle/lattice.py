@@ -52,7 +52,7 @@ D3Q19 = Lattice("D3Q19",
                    (1, -1, 0), (-1, 1, 0), (1, 0, -1), (-1, 0, 1), (0, 1, -1), (0, -1, 1)),
                 w=(1 / 3,) + (1 / 18,) * 6 + (1 / 36,) * 12, cs2=1 / 3)
 
-# §3, D2Q9 table (used by no workload of the coupled step; kept for the lattice pins)
+# §3, D2Q9 table, in the table's order (the 2D ripening workload's lattice for g, h^A, h^B)
 D2Q9 = Lattice("D2Q9",
                e=((0, 0, 0), (1, 0, 0), (0, 1, 0), (-1, 0, 0), (0, -1, 0),
                   (1, 1, 0), (-1, 1, 0), (-1, -1, 0), (1, -1, 0)),

@@ -58,6 +58,22 @@ def test_d3q19_matches_paper_table():
     assert len(set(L.D3Q19.e)) == 19
 
 
+# the velocity tables of §3 as printed (k = 0..18 and k = 0..8, in the tables' order)
+PAPER_D3Q19 = [(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1),
+               (1, 1, 0), (-1, -1, 0), (1, 0, 1), (-1, 0, -1), (0, 1, 1), (0, -1, -1),
+               (1, -1, 0), (-1, 1, 0), (1, 0, -1), (-1, 0, 1), (0, 1, -1), (0, -1, 1)]
+PAPER_D2Q9 = [(0, 0), (1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1)]
+
+
+def test_velocity_tables_in_the_papers_order():
+    assert list(L.D3Q19.e) == PAPER_D3Q19
+    assert [v[:2] for v in L.D2Q9.e] == PAPER_D2Q9 and all(v[2] == 0 for v in L.D2Q9.e)
+    assert list(L.D2Q9.w) == [4 / 9] + [1 / 9] * 4 + [1 / 36] * 4
+    # D3Q19 pairs each direction with its opposite at k +- 1 (k = 1, 3, ..., 17)
+    for k in range(1, 19, 2):
+        assert tuple(-c for c in PAPER_D3Q19[k]) == PAPER_D3Q19[k + 1]
+
+
 def test_derivatives_match_finite_differences():
     x = torch.linspace(-0.3, 1.3, 41, dtype=torch.float64)
     h = 1e-6
