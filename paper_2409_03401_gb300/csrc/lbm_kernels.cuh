@@ -246,7 +246,7 @@ __device__ __forceinline__ void force_velocity(const NodeT& nd, R phi, R gx, R g
     uz = R(3) * jz + R(0.5) * Fz;
 }
 
-// correctly rounded reciprocal (one MUFU-based sequence instead of a full division in FP32)
+// reciprocal rounded to nearest (__frcp_rn), cheaper than a full FP32 division
 __device__ __forceinline__ float recip(float v) { return __frcp_rn(v); }
 __device__ __forceinline__ double recip(double v) { return 1.0 / v; }
 
@@ -530,8 +530,8 @@ phi_kernel(const DevParams P, const StateView st, typename RealOf<T>::type* __re
 // chunk of z planes. At each plane z:
 //   fill(z + 1): every thread gathers the scalar populations (g, h^A, h^B) of its own
 //     column at plane z + 1, keeps them decoded in shared memory (double-buffered) with
-//     S and c - c_0^eq, and writes phi into a 4-plane ring; 84 threads add the ring's
-//     one-node halo.
+//     S (and c - c_0^eq with 16-bit storage), and writes phi into a 4-plane ring; 84
+//     threads add the ring's one-node halo.
 //   centre(z): gather the 19 f populations, take the scalar populations of plane z from
 //     shared memory, form the capillary stencil from the ring, collide and store f, then
 //     collide and store g, h^A, h^B (all stores local and coalesced).
