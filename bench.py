@@ -3,9 +3,9 @@
 Workload: 512^3 lattice, D3Q19 flow + D3Q7 phi, c^A, c^B, FP32 population storage,
 half-way bounce-back walls at the z ends, periodic in x and y, seeded droplets at
 volume fraction 0.2 with radii in [6, 16] (seed 3). One "step" is one coupled time
-step of the whole lattice (the phi pass of the capillary stencil plus the fused
-collide-and-stream kernel). The 21.5 GB state is far larger than the 129 MB L2, so
-no flush is needed between timed steps.
+step of the whole lattice: one launch of the fused collide-and-stream kernel, which
+computes the capillary stencil's phi itself. The state (two copies of 21.5 GB) is far
+larger than the 129 MB L2, so no flush is needed between timed steps.
 
 Prints one JSON line. --impl reference times the FP64 CPU oracle instead (the
 reference arm of this method), on a bounded slab of the same workload.
@@ -14,6 +14,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -138,6 +139,20 @@ def make_workload(n, device, storage="f32"):
     return p, fields, (phi0, cA0, cB0)
 
 
+def host_info():
+    """Core count and CPU model of the host the oracle is timed on."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.machine()}
+
+
 def cpu_baseline(init_fields, p, planes, steps):
     """The FP64 oracle, as it stands, on a z-slab of the same initial fields."""
     import torch
@@ -153,8 +168,9 @@ def cpu_baseline(init_fields, p, planes, steps):
     dt = time.perf_counter() - t0
     mlups = q.nodes * steps / dt / 1e6
     return {"value": mlups, "unit": "MLUPS", "cores": torch.get_num_threads(), "kind": "oracle",
-            "sample": f"{q.nx}x{q.ny}x{planes} slab (z {z0}..{z0 + planes - 1}) of the 512^3 initial fields, "
-                      f"walls at the slab ends, {steps} steps after 1 untimed, {dt:.1f} s"}
+            "sample": f"{q.nx}x{q.ny}x{planes} slab (z {z0}..{z0 + planes - 1}) of the {p.nx}x{p.ny}x{p.nz} "
+                      f"initial fields, walls at the slab ends, {steps} steps after 1 untimed, {dt:.1f} s",
+            "host": host_info()}
 
 
 def time_device(sim, steps, warmup, dist):
@@ -444,7 +460,7 @@ def reference(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": config_of(args, p, ws),
            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": torch.get_num_threads(),
-                            "kind": "oracle", "sample": sample},
+                            "kind": "oracle", "sample": sample, "host": host_info()},
            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 

@@ -26,6 +26,7 @@ def test_reference_arm_prints_one_contract_line():
     assert "workload" in out["config"]
     cb = out["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == out["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert cb["host"]["nproc"] >= cb["cores"] and cb["host"]["cpu_model"]
     e2e = out["e2e"]
     assert e2e["value"] == out["value"] and e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
     assert out["ms_per_step"] > 0
