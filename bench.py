@@ -148,7 +148,7 @@ def host_info():
             if ln.startswith("Model name:"):
                 model = ln.split(":", 1)[1].strip()
                 break
-    except (OSError, subprocess.SubprocessError):
+    except Exception:                    # a description only: never let it stop the benchmark
         pass
     return {"nproc": os.cpu_count(), "cpu_model": model or platform.machine()}
 
