@@ -56,14 +56,18 @@ def test_graph_on_the_launch_bound_couple():
     p, fields = configs.diffusion_couple(storage="f64")
     f = [t.cuda() for t in fields()]
     s = torch.cuda.Stream()
-    times = {}
-    for graph in (False, True):
-        sim = Simulation(p, *f, stream=s)
-        sim.step(200, graph=graph)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        sim.step(4000, graph=graph)
-        torch.cuda.synchronize()
-        times[graph] = (time.perf_counter() - t0) / 4000 * 1e6
+    sims = {graph: Simulation(p, *f, stream=s) for graph in (False, True)}
+    for graph, sim in sims.items():
+        sim.step(200, graph=graph)                   # warm-up; captures the graph
+    torch.cuda.synchronize()
+    # best of three alternating host-timed runs per mode, so that a moment of host
+    # contention on a shared machine does not decide the comparison
+    times = {False: float("inf"), True: float("inf")}
+    for _ in range(3):
+        for graph, sim in sims.items():
+            t0 = time.perf_counter()
+            sim.step(2000, graph=graph)
+            torch.cuda.synchronize()
+            times[graph] = min(times[graph], (time.perf_counter() - t0) / 2000 * 1e6)
     print(f"512 x 8 couple, FP64: {times[False]:.2f} us/step plain, {times[True]:.2f} us/step graph")
     assert times[True] < times[False]
