@@ -418,3 +418,59 @@ def test_laplace_pressure_of_a_sphere():
     assert abs(dp / (2.0 * sigma / R) - 1) < 0.1
     u = torch.sqrt(f["ux"] ** 2 + f["uy"] ** 2 + f["uz"] ** 2)
     assert float(u.max()) * (1.0 / 6.0) / sigma < 1e-2
+
+
+def _wave_phase(profile, k, L):
+    """(amplitude, shift) of profile ~ amp sin(k (x - shift)) by projection on sin and cos."""
+    x = torch.arange(L, dtype=torch.float64)
+    a = float((profile * torch.sin(k * x)).sum()) * 2 / L
+    b = float((profile * torch.cos(k * x)).sum()) * 2 / L
+    return math.hypot(a, b), math.atan2(-b, a) / k
+
+
+@pytest.mark.parametrize("lattice", ["D3Q7", "D3Q19"])
+def test_composition_is_advected_by_the_flow(lattice):
+    # phase 1 everywhere (phi = 1: no source, no capillary force) under a uniform buoyancy
+    # phi g: the fluid starts at rest and gains g per step (u_T = T g, Eq. 41 with the forcing
+    # of Eq. 36), and a sine wave of c^A rides on it through the c u / c_s^2 term of Eq. 51:
+    # it moves by sum_{n<T} u_n = g T (T - 1) / 2 and decays as exp(-D k^2 T)
+    L, T, gx, D, eps = 64, 400, 2e-5, 0.1, 1e-3
+    ce = ((0.3, 0.3), (0.4, 0.4))
+    p = LBMParams(nx=L, ny=4, nz=4, lattice=lattice, flow=True, W=3.0, lam=100.0, M_phi=0.12, c_eq=ce,
+                  M=((D, D), (D, D)), nu=0.1, sigma=1e-3, g=(gx, 0.0, 0.0))
+    k = 2 * math.pi / L
+    x = torch.arange(L, dtype=torch.float64)
+    phi = torch.ones(p.shape, dtype=torch.float64)
+    cA = (0.4 + eps * torch.sin(k * x)).reshape(1, 1, L).expand(p.shape).contiguous()
+    cB = torch.full(p.shape, 0.4, dtype=torch.float64)
+    o = OracleLBM(p)
+    o.init(phi, cA, cB)
+    o.step(T)
+    f = o.fields()
+    assert float((f["phi"] - 1).abs().max()) < 1e-14
+    assert abs(float(f["ux"].mean()) - T * gx) < 1e-12 and float(f["ux"].std()) < 1e-14
+    amp, shift = _wave_phase(f["cA"][0, 0] - f["cA"][0, 0].mean(), k, L)
+    assert abs(shift - gx * T * (T - 1) / 2) < 0.01                 # of 1.596 nodes
+    assert abs(amp / eps / math.exp(-D * k * k * T) - 1) < 2e-3
+
+
+def test_phase_field_is_advected_by_the_flow():
+    # the phi equation alone (source off, sigma = 0): a small sine wave of phi around 1/2 under
+    # buoyancy phi g moves with the mean velocity 0.5 g n through the phi u / c_s^2 term of
+    # Eq. 47 and decays as exp(-M_phi k^2 T); the wave itself makes the force slightly
+    # non-uniform, so the shift is held to 0.03 of its 1.596 nodes
+    L, T, gx, Mphi, eps = 64, 400, 4e-5, 0.05, 1e-3
+    ce = ((0.3, 0.3), (0.4, 0.4))
+    p = LBMParams(nx=L, ny=4, nz=4, lattice="D3Q7", flow=True, W=3.0, lam=100.0, M_phi=Mphi, c_eq=ce,
+                  M=((0.1, 0.1), (0.1, 0.1)), nu=0.1, sigma=0.0, g=(gx, 0.0, 0.0), source_off=True)
+    k = 2 * math.pi / L
+    x = torch.arange(L, dtype=torch.float64)
+    phi = (0.5 + eps * torch.sin(k * x)).reshape(1, 1, L).expand(p.shape).contiguous()
+    c = torch.full(p.shape, 0.35, dtype=torch.float64)
+    o = OracleLBM(p)
+    o.init(phi, c, c.clone())
+    o.step(T)
+    f = o.fields()
+    amp, shift = _wave_phase(f["phi"][0, 0] - f["phi"][0, 0].mean(), k, L)
+    assert abs(shift - 0.5 * gx * T * (T - 1) / 2) < 0.03
+    assert abs(amp / eps / math.exp(-Mphi * k * k * T) - 1) < 2e-3
