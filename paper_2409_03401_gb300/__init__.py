@@ -4,10 +4,10 @@ phase-field model for two-phase ternary fluids with flow.
 The compute path is the CUDA library liblbm_gb300.so behind the C-ABI of
 include/lbm.h; ``Simulation`` binds it to torch-owned device memory.
 """
-from .lattice import Simulation
+from .lattice import Simulation, droplet_stats
 from ._lib import LBMError
 
-__all__ = ["Simulation", "LBMError", "build"]
+__all__ = ["Simulation", "LBMError", "droplet_stats", "build"]
 
 
 def build(force=False):

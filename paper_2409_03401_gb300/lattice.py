@@ -5,6 +5,7 @@ device, binds them with lbm_init, and forwards lbm_step / lbm_fields / lbm_reduc
 Every step of the method runs in the sm_103a kernels of liblbm_gb300.so.
 """
 import ctypes
+import math
 
 import torch
 
@@ -13,6 +14,21 @@ from . import _lib
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
+
+
+def droplet_stats(sums, two_d):
+    """Droplet count N (the Euler characteristic of the reduction) and mean radius <R> from
+    the interface measure A = sum (4/W) phi (1 - phi): <R> = A / (2 pi N) in 2D (Eq. 67),
+    sqrt(A / (4 pi N)) in 3D (sum of sphere areas). <R> is NaN when N <= 0."""
+    n = sums["euler"]
+    a = sums["interface"]
+    if n <= 0:
+        r = float("nan")
+    elif two_d:
+        r = a / (2.0 * math.pi * n)
+    else:
+        r = math.sqrt(a / (4.0 * math.pi * n))
+    return {"N": n, "R_mean": r, "interface": a}
 
 
 class Simulation:
@@ -139,6 +155,11 @@ class Simulation:
         if st != _lib.LBM_OK and (raise_unstable or st != _lib.LBM_ERR_UNSTABLE):
             _lib.check(st, self._ctx)
         return {k: buf[i] for i, k in enumerate(_lib.REDUCTIONS)}
+
+    def droplets(self):
+        """Droplet count N and mean radius <R> of the current time level (§4.2.2, one
+        reduction pass on the device; synchronises the stream)."""
+        return droplet_stats(self.sums(), self.params.lattice in ("D2Q5", "D2Q9"))
 
     def profile_begin(self, max_steps):
         """Record CUDA events around this context's kernels for the next max_steps steps."""

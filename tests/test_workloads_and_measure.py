@@ -150,3 +150,24 @@ def test_euler_counts_droplets(walls):
     n = measure.count_droplets(phi, walls)
     assert n == len(radii) > 10
     assert measure.euler_characteristic(phi, walls) == n
+
+
+@pytest.mark.parametrize("dims", [2, 3])
+def test_droplet_stats_of_the_binding_match_the_oracle(dims):
+    # the package's <R> and N from the reduction's two outputs, fed here with the oracle's
+    # Euler characteristic and interface measure of a known droplet field
+    from paper_2409_03401_gb300 import droplet_stats
+    W = 3.0
+    if dims == 3:
+        shape = (40, 36, 44)
+        centres, radii = place_droplets(shape, 0.1, 4.0, 7.0, W, seed=5)
+    else:
+        shape = (1, 96, 110)
+        centres, radii = place_droplets(shape, 0.1, 4.0, 9.0, W, seed=5)
+    phi = phi_field(shape, centres, radii, W).numpy()
+    sums = {"euler": float(measure.euler_characteristic(phi)), "interface": measure.interface_measure(phi, W)}
+    got = droplet_stats(sums, two_d=(dims == 2))
+    R, n = measure.mean_radius(phi, W)
+    assert got["N"] == n == len(radii)
+    assert abs(got["R_mean"] - R) < 1e-12 * R
+    assert math.isnan(droplet_stats({"euler": 0.0, "interface": 1.0}, two_d=False)["R_mean"])
