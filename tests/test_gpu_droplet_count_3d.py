@@ -83,6 +83,7 @@ def test_droplet_fields(kind, storage):
         n = measure.count_droplets(phi, _walls(p))
         assert n > 5
         assert sim.sums()["euler"] == float(chi) == float(n)
+        assert sim.droplets()["N"] == float(n)
 
 
 def test_static_reduce_counts_too():
