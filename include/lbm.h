@@ -147,8 +147,9 @@ lbm_status lbm_init(const lbm_params* p, void* d_state, void* d_work,
                     const double* d_phi0, const double* d_cA0, const double* d_cB0,
                     void* stream, lbm_ctx** out);
 
-/* Bind buffers whose state was written earlier (checkpoint/resume): d_state must hold
- * a state produced by this library for the same parameters at time t. No kernel runs. */
+/* Bind buffers whose state was written earlier (checkpoint/resume; the paper describes
+ * none): d_state must hold a state produced by this library for the same parameters at
+ * time t. No kernel runs. */
 lbm_status lbm_attach(const lbm_params* p, void* d_state, void* d_work, int64_t t,
                       void* stream, lbm_ctx** out);
 
@@ -175,11 +176,14 @@ int64_t lbm_time(const lbm_ctx* ctx);
  * mu by Eq. 33, c by Eq. 52, p by Eq. 40, u by Eq. 41 (0 without flow). Asynchronous. */
 lbm_status lbm_fields(lbm_ctx* ctx, void* const* dst);
 
-/* FP64 global diagnostics of the current time level into host memory out[LBM_NRED].
- * Synchronises the stream. Returns LBM_ERR_UNSTABLE if a moment is not finite. */
+/* FP64 global diagnostics of the current time level into host memory out[LBM_NRED]: the
+ * sums of Eqs. 40, 49, 52, max |u| (§4.2.4), the interface measure of Eq. 67 and the droplet
+ * count of §4.2.2 (LBM_RED_*). Synchronises the stream. Returns LBM_ERR_UNSTABLE if a
+ * moment is not finite. */
 lbm_status lbm_reduce(lbm_ctx* ctx, double* out);
 
-/* Kernel timing on the context's stream. lbm_profile_begin(ctx, max_steps) creates
+/* Kernel timing on the context's stream (no counterpart in the paper).
+ * lbm_profile_begin(ctx, max_steps) creates
  * 3 * max_steps CUDA events (host-side driver objects, no device memory); each of the
  * next max_steps steps records one event before, between and after its kernels.
  * lbm_profile_end synchronises the stream and writes out[0] = total ms of the phi
@@ -192,7 +196,7 @@ lbm_status lbm_profile_end(lbm_ctx* ctx, double* out);
  * copies and the scalar lattice is LBM_D3Q7 (the fused kernel), else 1; 0 for NULL. */
 int lbm_kernels_per_step(const lbm_ctx* ctx);
 
-/* One step out of place, without a context: d_src holds one state copy at time t (the
+/* One step (§3) out of place, without a context: d_src holds one state copy at time t (the
  * layout lbm_init writes: lbm_copy_bytes bytes), d_dst receives time t + 1 in the same
  * layout; d_src is not modified. d_work as for lbm_init (used by in-place flow). The
  * adjoint's recompute pass uses it to rebuild the states of a segment from a checkpoint. */
