@@ -32,6 +32,8 @@ from .droplets import place_droplets, phi_field, composition_fields, planar_coup
 
 LAMBDA_COUPLE = 60.0
 M_PHI_COUPLE = 0.12
+# matrix composition c_0^eq + delta (c_1^eq - c_0^eq) of the 3D workloads (the 2D workload
+# takes the 2D table's delta = 0.1; the paper's 3D table has delta = 0.2)
 SUPERSATURATION = 0.02
 
 
