@@ -30,7 +30,7 @@ N = 512
 # four rest populations g_0, h^A_0, h^B_0, f_0 in FP32 (36 x 2 B + 4 x 4 B = 88 B each way)
 ALG_BYTES_PER_NODE = {"f32": 320.0, "f16": 176.0, "bf16": 176.0, "f64": 640.0}
 # DRAM bytes (read + write) per node of one fused_flow_kernel<float> launch, from an ncu capture
-# of this kernel at 192^3 (profiles/fused_flow_kernel_f32_192cube.md); traffic scales with the
+# of this kernel at 192^3; traffic scales with the
 # node count. Set to None whenever the kernel changes until it is captured again.
 NCU_DRAM_BYTES_PER_NODE_F32 = 164.98 + 153.87
 

@@ -47,12 +47,22 @@ typedef enum {
 typedef enum { LBM_D2Q5 = 0, LBM_D3Q7 = 1, LBM_D3Q19 = 2, LBM_D2Q9 = 3 } lbm_lattice;
 
 /* Storage type of the populations. Arithmetic is FP64 for LBM_F64 and FP32 otherwise.
- * LBM_F16 / LBM_BF16 store every moving population as a 16-bit deviation from its
- * lattice-weight reference, q_k = P_k / w_k - ref (f: ref 0 times f_scale; g: ref 1/2;
- * h: ref 0 times 64); the rest populations g_0, h^A_0, h^B_0, f_0 stay FP32. Every step sets
- * each rest population to its set's conserved total at the node (p_h, phi~ + S, c - c_0^eq)
- * minus the moving populations as stored, so the node's sums (phi, c^A, c^B, p_h) are
- * carried to FP32 accuracy and 16-bit rounding cannot act as a source.
+ * LBM_F16 / LBM_BF16 store every moving population (k > 0) in 16 bits as its value per unit
+ * weight: x_k = g_k / w_k - 1/2, x_k = h_k / w_k, and for f the deviation from the rest
+ * population of the node that stored it, x_k = f_k / w_k - f_0 / w_0 (f_0 ~ w_0 p_h, so the
+ * pressure is not rounded). The rest populations g_0, h^A_0, h^B_0, f_0 stay FP32 (in place,
+ * f_0 alternates between two planes by the parity of the time level).
+ *   LBM_F16: g in 16-bit fixed point over [-1, 1) (step 2^-15); f (as 8 x) and h in a 16-bit
+ *            float with 1 sign, 4 exponent and 11 mantissa bits, exponent bias 15, subnormals,
+ *            no infinities (the "FP16C" layout of Lehmann et al., Phys. Rev. E 106, 015308,
+ *            2022). Both saturate: |u| must stay below about 0.15 and |h_k / w_k| below 2,
+ *            far outside the regime of a stable run.
+ *   LBM_BF16: every x_k as BF16 (8-bit significand).
+ * Every step sets the rest populations of g and h to their set's conserved total at the node
+ * (phi~ + S, c - c_0^eq) minus the moving populations as stored, so phi, c^A and c^B are
+ * carried to FP32 accuracy and 16-bit rounding cannot act as a source of composition; the
+ * f_0 of a node is its collided value, so sum p_h carries the 16-bit rounding of the moving
+ * f (the pressure is defined up to a constant in the incompressible limit).
  * In every storage type the rest populations h^alpha_0 are kept shifted by the constant
  * c_0^{alpha,eq} (h_0 - c_0^eq), so that the sum of the h populations is c - c_0^eq and
  * mu (Eq. 33) does not inherit the rounding of c itself. */
@@ -87,7 +97,7 @@ typedef struct lbm_params {
     double nu;               /* kinematic viscosity, tau_f = nu / c_s^2 (Eq. 36) */
     double sigma;            /* surface tension in Eq. 34 */
     double g[3];             /* buoyancy per unit phi: F_g = phi * g (§2.5, Delta rho g / rho_0) */
-    double f_scale;          /* 16-bit storage scale of f_k / w_k: 0 or 1024 (fixed at 1024) */
+    double f_scale;          /* reserved: 0 or 1024 (the 16-bit formats have fixed scales) */
     int32_t collision;       /* flow collision, lbm_collision: LBM_BGK (Eq. 36), LBM_TRT or LBM_MRT */
     double trt_magic;        /* LBM_TRT: Lambda = (1/omega+ - 1/2)(1/omega- - 1/2) > 0, where omega+
                               * is the BGK rate of Eq. 36 (it sets nu); 0 selects 3/16 */
@@ -250,22 +260,94 @@ lbm_status lbm_adjoint_init(const lbm_params* p, const double* d_phi0, const dou
  * Synchronises the stream. */
 lbm_status lbm_adjoint_theta(const lbm_params* p, void* d_adj_work, double* out, void* stream);
 
+/* ------------------------------------------------------------------------------------
+ * Slabs: a 3D lattice decomposed along z, the paper's domain decomposition for its
+ * multi-GPU runs (§3; §4.2.4 ran 2048 x 512 x 512 on 64 GPUs). A slab owns the planes
+ * [z0, z0 + nzl) of the lattice p describes and keeps one ghost plane on each side that has
+ * a neighbour (another slab, or, where z is periodic, the slab across the periodic end; a
+ * single slab covering a periodic lattice is its own neighbour). Slabs always use the
+ * two-buffer layout (p->inplace must be 0); with flow and D3Q7 the step is the fused kernel.
+ * The arithmetic per node is that of the undivided lattice, so a decomposed run equals it
+ * bit for bit once the halos are exchanged as below.
+ *
+ * One step of the decomposed lattice, for every slab:
+ *   1. lbm_step(ctx, 1) (a slab advances one step per call; larger counts are refused);
+ *   2. populations: lbm_slab_pack(ctx, 0, m0) and lbm_slab_pack(ctx, 1, m1) write the
+ *      populations that leave through the lower and upper face (5 flow and 1 or 5 per
+ *      scalar set per face node; with 16-bit storage and flow also the FP32 f_0 of the edge
+ *      plane, the reference of those f); the lower neighbour unpacks m0 at its side 1
+ *      (lbm_slab_unpack(nbr, 1, m0)), the upper one m1 at its side 0;
+ *   3. phi (flow only): after step 2, lbm_slab_phi_pack(ctx, side, buf) writes phi of the
+ *      lowest (side 0) or highest (side 1) own plane; the neighbour on that side stores it
+ *      with lbm_slab_phi_unpack at its opposite side. The capillary stencil of the edge
+ *      planes reads it at the next step.
+ * After lbm_slab_init only step 3 is needed before the first step (init places the ghost
+ * populations itself). Messages are device buffers of lbm_slab_halo_bytes and
+ * lbm_slab_phi_bytes; how they travel (a device copy, NCCL send/recv) is the caller's. */
+
+/* Planes of a slab's own lattice (nzl plus its ghost planes); 0 for invalid arguments. The
+ * initial fields of lbm_slab_init and the outputs of lbm_fields on a slab have this many z
+ * planes: the global planes z0 - 1 .. z0 + nzl (wrapped at periodic ends; a plane beyond a
+ * wall is not included). */
+int32_t lbm_slab_planes(const lbm_params* p, int32_t z0, int32_t nzl);
+
+/* Bytes of a slab's state (two copies of its own lattice) and work buffers; 0 for invalid
+ * arguments. */
+size_t lbm_slab_state_bytes(const lbm_params* p, int32_t z0, int32_t nzl);
+size_t lbm_slab_work_bytes(const lbm_params* p, int32_t z0, int32_t nzl);
+
+/* Initialise the slab [z0, z0 + nzl) of lattice p from FP64 fields over its lbm_slab_planes
+ * planes (nx-fastest, the ghost planes included: the initial capillary stencil reads them).
+ * Buffers as for lbm_init. On a slab context lbm_step takes at most one step per call,
+ * lbm_step_graph and the adjoint are refused, lbm_fields writes the own planes of arrays
+ * shaped like the initial fields, and lbm_reduce sums the own planes (its droplet count,
+ * which needs the whole lattice, is 0). */
+lbm_status lbm_slab_init(const lbm_params* p, int32_t z0, int32_t nzl, void* d_state, void* d_work,
+                         const double* d_phi0, const double* d_cA0, const double* d_cB0, void* stream,
+                         lbm_ctx** out);
+
+/* Ghost planes of a slab context: bit 0 set when a neighbour lies below, bit 1 above; -1 if
+ * ctx is not a slab. */
+int32_t lbm_slab_ghosts(const lbm_ctx* ctx);
+
+/* Size of one population message (both faces have the same) and of one phi message; 0 if
+ * ctx is not a slab. */
+size_t lbm_slab_halo_bytes(const lbm_ctx* ctx);
+size_t lbm_slab_phi_bytes(const lbm_ctx* ctx);
+
+/* Step 2 of the exchange: pack the populations leaving through face side (0 lower, 1 upper)
+ * at the current time level into d_msg; unpack a neighbour's message into the ghost plane
+ * on side (0: the message of the lower neighbour's upper face). Asynchronous on the
+ * context's stream (device-to-device copies). LBM_ERR_STATE when the side has no
+ * neighbour (a wall) or ctx is not a slab. */
+lbm_status lbm_slab_pack(lbm_ctx* ctx, int32_t side, void* d_msg);
+lbm_status lbm_slab_unpack(lbm_ctx* ctx, int32_t side, const void* d_msg);
+
+/* Step 3: phi (Eq. 49, storage's arithmetic type) of the edge plane on side at the current
+ * time level into d_phi (nx * ny values, x fastest; needs the ghost populations of step 2);
+ * store a neighbour's edge-plane phi as the ghost phi on side. */
+lbm_status lbm_slab_phi_pack(lbm_ctx* ctx, int32_t side, void* d_phi);
+lbm_status lbm_slab_phi_unpack(lbm_ctx* ctx, int32_t side, const void* d_phi);
+
 /* Allocation-free FP64 diagnostics. The paper has no counterpart: this is for callers that
  * cannot allocate device memory at the time they need the sums (for example a host
  * application that hands this library its state buffer but owns every allocation, or a
  * real-time loop where allocation is forbidden after start-up). Same results as
  * lbm_reduce for the state copy d_state holds at time t (the buffer lbm_init was given),
- * but the reduction's scratch (block partials, results, for flow or 2D lattices the phi
- * field, for 3D lattices one bit per node) lives
- * in a file-scope device array of 4 MiB that every GPU loading this library holds until
- * the process exits. Lattices whose scratch exceeds 4 MiB (flow or 2D lattices above about
- * one million nodes, 3D lattices without flow above about 33 million) are rejected with
- * LBM_ERR_ARG. The call allocates nothing. The first call
- * on each device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture. Every call shares the
- * array and leaves its contents behind; the kernels overwrite all of it that they read, so
- * nothing needs clearing, but calls that overlap on the GPU (other streams, other host
- * threads) race on it. Synchronises the stream. */
+ * but the reduction's scratch (block partials and results; for flow or 2D lattices the phi
+ * field, 4 bytes per node, 8 with LBM_F64; for 3D lattices one bit per node) lives in a
+ * file-scope device array of 4 MiB that every GPU loading this library holds until the
+ * process exits. After the 97 KB of partials the array holds the phi field of about
+ * 1.02 million nodes (FP32 and 16-bit storage) or 0.51 million (LBM_F64), and the bit field
+ * of about 33.5 million nodes (3D lattices without flow); larger lattices are rejected with
+ * LBM_ERR_ARG before any launch. The call allocates nothing. d_state and the stream must
+ * belong to the current device (LBM_ERR_ARG otherwise): the array's address is looked up,
+ * with cudaGetSymbolAddress, for the current device on every call, so the very first call
+ * on a device also loads the library's module there. Every call synchronises the stream and
+ * copies the sums to the host, so it cannot be made while its stream is being captured into
+ * a graph. Every call shares the array and leaves its contents behind; the kernels
+ * overwrite all of it that they read, so nothing needs clearing, but calls that overlap on
+ * the GPU (other streams, other host threads) race on it. */
 lbm_status lbm_reduce_static(const lbm_params* p, const void* d_state, int64_t t, double* out, void* stream);
 
 /* Release the context (host memory only; device buffers remain the caller's). */

@@ -83,6 +83,17 @@ def load():
         "lbm_adjoint_init": (ctypes.c_int, [P, vp, vp, vp, vp, vp, vp, vp]),
         "lbm_adjoint_theta": (ctypes.c_int, [P, vp, ctypes.POINTER(ctypes.c_double), vp]),
         "lbm_reduce_static": (ctypes.c_int, [P, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), vp]),
+        "lbm_slab_planes": (ctypes.c_int32, [P, ctypes.c_int32, ctypes.c_int32]),
+        "lbm_slab_state_bytes": (ctypes.c_size_t, [P, ctypes.c_int32, ctypes.c_int32]),
+        "lbm_slab_work_bytes": (ctypes.c_size_t, [P, ctypes.c_int32, ctypes.c_int32]),
+        "lbm_slab_init": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, vp, vp, vp, vp, vp, vp, ctx_pp]),
+        "lbm_slab_ghosts": (ctypes.c_int32, [vp]),
+        "lbm_slab_halo_bytes": (ctypes.c_size_t, [vp]),
+        "lbm_slab_phi_bytes": (ctypes.c_size_t, [vp]),
+        "lbm_slab_pack": (ctypes.c_int, [vp, ctypes.c_int32, vp]),
+        "lbm_slab_unpack": (ctypes.c_int, [vp, ctypes.c_int32, vp]),
+        "lbm_slab_phi_pack": (ctypes.c_int, [vp, ctypes.c_int32, vp]),
+        "lbm_slab_phi_unpack": (ctypes.c_int, [vp, ctypes.c_int32, vp]),
         "lbm_last_error": (ctypes.c_char_p, [vp]),
         "lbm_build_info": (ctypes.c_char_p, []),
     }
@@ -100,7 +111,10 @@ def exported_symbols():
             "lbm_fields", "lbm_reduce", "lbm_profile_begin", "lbm_profile_end", "lbm_kernels_per_step",
             "lbm_copy_bytes", "lbm_step_buffers", "lbm_adjoint_bytes", "lbm_adjoint_work_bytes",
             "lbm_adjoint_reset", "lbm_adjoint_seed", "lbm_adjoint_step", "lbm_adjoint_segment", "lbm_adjoint_init",
-            "lbm_adjoint_theta", "lbm_reduce_static", "lbm_destroy", "lbm_last_error", "lbm_build_info"]
+            "lbm_adjoint_theta", "lbm_reduce_static", "lbm_slab_planes", "lbm_slab_state_bytes",
+            "lbm_slab_work_bytes", "lbm_slab_init", "lbm_slab_ghosts", "lbm_slab_halo_bytes", "lbm_slab_phi_bytes",
+            "lbm_slab_pack", "lbm_slab_unpack", "lbm_slab_phi_pack", "lbm_slab_phi_unpack", "lbm_destroy",
+            "lbm_last_error", "lbm_build_info"]
 
 
 def check(status, ctx=None):

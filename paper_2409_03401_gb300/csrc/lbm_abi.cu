@@ -1,7 +1,6 @@
 // C-ABI entry points (include/lbm.h): validation, buffer layout, launch sequencing.
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -37,6 +36,7 @@ struct Layout {
     size_t state = 0, work = 0;
     size_t off_f = 0, off_g = 0, off_hA = 0, off_hB = 0, off_rest = 0;
     size_t off_phi = 0, off_bits = 0, off_partials = 0, off_out = 0;
+    size_t off_phig[2] = {0, 0};   // slab: phi of the neighbours' edge planes (below, above)
 };
 
 const char* check_params(const lbm_params* p) {
@@ -66,7 +66,8 @@ const char* check_params(const lbm_params* p) {
     return nullptr;
 }
 
-Layout layout_of(const lbm_params* p) {
+// slab: two state copies always, and two ghost phi planes in the work buffer
+Layout layout_of(const lbm_params* p, bool slab = false) {
     Layout L;
     L.n = (long long)p->nx * p->ny * p->nz;
     L.plane = round_up(L.n, 128);
@@ -78,9 +79,11 @@ Layout layout_of(const lbm_params* p) {
     L.off_g = o;  o += Q * pb;
     L.off_hA = o; o += Q * pb;
     L.off_hB = o; o += Q * pb;
-    L.off_rest = o; o += is16(p->storage) ? 4 * (size_t)L.plane * sizeof(float) : 0;
+    // FP32 rest populations of 16-bit storage: g_0, hA_0, hB_0, f_0 (and f_0 of odd time levels
+    // in place, see lbm::Addr)
+    L.off_rest = o; o += is16(p->storage) ? 5 * (size_t)L.plane * sizeof(float) : 0;
     L.copy = round_up(o, kAlign);
-    L.two = p->flow && !p->inplace;
+    L.two = slab || (p->flow && !p->inplace);
     L.state = L.copy * (L.two ? 2 : 1);
     const size_t real = p->storage == LBM_F64 ? 8 : 4;
     size_t w = 0;
@@ -90,6 +93,10 @@ Layout layout_of(const lbm_params* p) {
     L.off_bits = w;     w += two_d(p->lattice) ? 0 : round_up((size_t)((L.n + 31) / 32) * sizeof(unsigned), kAlign);
     L.off_partials = w; w += round_up((size_t)kRedBlocks * LBM_NRED * sizeof(double), kAlign);
     L.off_out = w;      w += round_up(LBM_NRED * sizeof(double), kAlign);
+    for (int i = 0; i < 2; ++i) {
+        L.off_phig[i] = w;
+        w += slab ? round_up((size_t)p->nx * p->ny * real, kAlign) : 0;
+    }
     L.work = w;
     return L;
 }
@@ -117,6 +124,9 @@ DevParams dev_params(const lbm_params* p, const Layout& L) {
     DevParams d{};
     d.nx = p->nx; d.ny = p->ny; d.nz = p->nz;
     d.wall_x = p->wall_x != 0; d.wall_z = p->wall_z != 0; d.source_off = p->source_off != 0;
+    d.wall_zlo = d.wall_zhi = d.wall_z;
+    d.z_lo = 0;
+    d.z_hi = p->nz;
     d.n = L.n; d.plane = L.plane;
     d.W = p->W; d.lam = p->lambda;
     d.kphi = p->M_phi / (p->W * p->W);
@@ -166,6 +176,10 @@ struct lbm_ctx {
     std::vector<cudaEvent_t> ev;   // profiling: 3 events per timed step
     int prof_max = 0, prof_n = 0;
     cudaGraphExec_t graph = nullptr;   // two steps captured from an even time level
+    // slab of a z-decomposed lattice (lbm_slab_init): global first plane, own planes, and
+    // whether a neighbour's plane sits below / above (ghost planes z_lo - 1 and z_hi)
+    bool slab = false;
+    int z0 = 0, nzl = 0, glo = 0, ghi = 0;
 };
 
 namespace {
@@ -308,6 +322,18 @@ lbm_status lbm_attach(const lbm_params* p, void* d_state, void* d_work, int64_t 
 }
 
 namespace {
+// Slab: copy the neighbours' edge-plane phi (received by lbm_slab_phi_unpack) into the phi
+// field's planes z_lo - 1 and z_hi, where the per-node kernels' stencil reads it.
+void ghost_phi_to_field(lbm_ctx* c) {
+    const size_t real = c->p.storage == LBM_F64 ? 8 : 4;
+    const size_t pb = (size_t)c->p.nx * c->p.ny * real;
+    char* phi = c->work + c->L.off_phi;
+    if (c->glo) cudaMemcpyAsync(phi + (size_t)(c->dp.z_lo - 1) * pb, c->work + c->L.off_phig[0], pb,
+                                cudaMemcpyDeviceToDevice, c->stream);
+    if (c->ghi) cudaMemcpyAsync(phi + (size_t)c->dp.z_hi * pb, c->work + c->L.off_phig[1], pb,
+                                cudaMemcpyDeviceToDevice, c->stream);
+}
+
 // Queue the kernels that advance time level t to t + 1 (no change to the context).
 void launch_one(lbm_ctx* c, int64_t t, cudaEvent_t* e) {
     const int mode = c->L.two ? lbm::kModePull : ((t & 1) ? lbm::kModeAAOdd : lbm::kModeAAEven);
@@ -318,6 +344,7 @@ void launch_one(lbm_ctx* c, int64_t t, cudaEvent_t* e) {
     const bool fused = c->L.two && fused_flow(&c->p);
     if (c->p.flow && !fused) {
         LBM_DISPATCH(c->p.storage, launch_phi, c->dp, src, c->p.lattice, mode, c->work + c->L.off_phi, c->stream);
+        if (c->slab) ghost_phi_to_field(c);
     }
     if (e) cudaEventRecord(e[1], c->stream);
     if (fused) {
@@ -333,6 +360,8 @@ void launch_one(lbm_ctx* c, int64_t t, cudaEvent_t* e) {
 lbm_status lbm_step(lbm_ctx* c, int nsteps) {
     if (!c) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
     if (nsteps < 0) return fail(c, LBM_ERR_ARG, "nsteps must be >= 0");
+    if (c->slab && nsteps > 1)
+        return fail(c, LBM_ERR_STATE, "a slab advances one step per call: exchange its halos between steps");
     cudaGetLastError();
     for (int i = 0; i < nsteps; ++i) {
         const bool timed = c->prof_n < c->prof_max;
@@ -348,6 +377,7 @@ lbm_status lbm_step_graph(lbm_ctx* c, int nsteps) {
     if (nsteps < 0) return fail(c, LBM_ERR_ARG, "nsteps must be >= 0");
     if (c->stream == nullptr || c->stream == cudaStreamLegacy || c->stream == cudaStreamPerThread)
         return fail(c, LBM_ERR_ARG, "graph replay needs a created (capturable) stream, not a default stream");
+    if (c->slab) return fail(c, LBM_ERR_STATE, "graph replay of two steps does not apply to a slab");
     if (nsteps == 0) return LBM_OK;
     if (c->t & 1) {                                  // align to an even time level
         lbm_status s = lbm_step(c, 1);
@@ -429,6 +459,7 @@ lbm_status lbm_fields(lbm_ctx* c, void* const* dst) {
     lbm::FieldPtrs fp;
     for (int i = 0; i < LBM_NFIELDS; ++i) fp.p[i] = dst[i];
     cudaGetLastError();
+    if (c->slab && c->p.flow) ghost_phi_to_field(c);
     LBM_DISPATCH(c->p.storage, launch_fields, c->dp, current(c), c->p.lattice, c->p.flow != 0, read_mode(c),
                  c->work + c->L.off_phi, fp, c->stream);
     return cuda_check(c, "fields kernel launch");
@@ -440,8 +471,11 @@ lbm_status lbm_reduce(lbm_ctx* c, double* out) {
     cudaGetLastError();
     double* partials = reinterpret_cast<double*>(c->work + c->L.off_partials);
     double* dout = reinterpret_cast<double*>(c->work + c->L.off_out);
+    if (c->slab && c->p.flow) ghost_phi_to_field(c);
+    // a slab keeps no bit field: its droplet count (LBM_RED_EULER) is left at 0
     LBM_DISPATCH(c->p.storage, launch_reduce, c->dp, current(c), c->p.lattice, c->p.flow != 0, read_mode(c),
-                 c->work + c->L.off_phi, c->work + c->L.off_bits, partials, kRedBlocks, c->stream);
+                 c->work + c->L.off_phi, c->slab ? nullptr : c->work + c->L.off_bits, partials, kRedBlocks,
+                 c->stream);
     reduce_final<<<1, 256, 0, c->stream>>>(partials, kRedBlocks, dout);
     lbm_status s = cuda_check(c, "reduce kernel launch");
     if (s != LBM_OK) return s;
@@ -587,6 +621,189 @@ lbm_status lbm_adjoint_theta(const lbm_params* p, void* d_adj_work, double* out,
     return LBM_OK;
 }
 
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------
+// Slabs of a lattice decomposed along z (the paper's domain decomposition, §3).
+namespace {
+
+const char* check_slab(const lbm_params* p, int z0, int nzl) {
+    if (const char* m = check_params(p)) return m;
+    if (two_d(p->lattice)) return "slabs split a 3D lattice along z";
+    if (p->inplace) return "slabs use the two-buffer layout (inplace must be 0)";
+    if (z0 < 0 || nzl < 1 || (long long)z0 + nzl > p->nz) return "slab planes [z0, z0 + nzl) must lie in [0, nz)";
+    return nullptr;
+}
+
+// The slab's own lattice: its planes plus one ghost plane on each side that has a
+// neighbour (another slab, or the slab itself across a periodic end).
+lbm_params slab_lattice(const lbm_params* p, int z0, int nzl, int& glo, int& ghi) {
+    glo = (z0 > 0 || !p->wall_z) ? 1 : 0;
+    ghi = (z0 + nzl < p->nz || !p->wall_z) ? 1 : 0;
+    lbm_params q = *p;
+    q.nz = nzl + glo + ghi;
+    return q;
+}
+
+// Slot planes of one set whose velocity has z component ez (in the lattice's order).
+template <class Lat>
+void slots_with_ez(int Q, int ez, int first, std::vector<int>& out) {
+    for (int k = 1; k < Q; ++k)
+        if (Lat::ez(k) == ez) out.push_back(first + k);
+}
+
+// Pieces of one face message: (population plane, element size); -1 stands for the FP32 f_0
+// plane of 16-bit storage, the reference of the moving f (Codec16Pop).
+std::vector<int> face_planes(const lbm_params* p, int ez) {
+    std::vector<int> v;
+    if (p->flow) slots_with_ez<lbm::D3Q19>(19, ez, 0, v);
+    const int Q = scalar_q(p->lattice);
+    for (int set = 0; set < 3; ++set) {
+        if (p->lattice == LBM_D3Q19) slots_with_ez<lbm::Scalar<lbm::LAT_D3Q19>>(Q, ez, 19 + set * Q, v);
+        else slots_with_ez<lbm::Scalar<lbm::LAT_D3Q7>>(Q, ez, 19 + set * Q, v);
+    }
+    if (p->flow && is16(p->storage)) v.push_back(-1);
+    return v;
+}
+
+size_t face_bytes(const lbm_params* p) {
+    const size_t nxy = (size_t)p->nx * p->ny;
+    size_t b = 0;
+    for (int k : face_planes(p, 1)) b += nxy * (k < 0 ? sizeof(float) : storage_size(p->storage));
+    return b;
+}
+
+// Copy plane z of every piece between the state copy st and a packed message.
+lbm_status face_copy(lbm_ctx* c, const StateView& st, int ez, int z, void* msg, bool pack) {
+    const size_t nxy = (size_t)c->p.nx * c->p.ny;
+    const size_t es = storage_size(c->p.storage);
+    char* m = static_cast<char*>(msg);
+    for (int k : face_planes(&c->p, ez)) {
+        const size_t eb = k < 0 ? sizeof(float) : es;
+        char* plane = k < 0 ? reinterpret_cast<char*>(st.rest + 3 * c->L.plane) : static_cast<char*>(st.plane[k]);
+        char* at = plane + (size_t)z * nxy * eb;
+        cudaError_t e = pack ? cudaMemcpyAsync(m, at, nxy * eb, cudaMemcpyDeviceToDevice, c->stream)
+                             : cudaMemcpyAsync(at, m, nxy * eb, cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) return fail(c, LBM_ERR_CUDA, std::string("slab halo copy: ") + cudaGetErrorString(e));
+        m += nxy * eb;
+    }
+    return LBM_OK;
+}
+
+lbm_status check_side(lbm_ctx* c, int side, const void* buf) {
+    if (!c) return fail(nullptr, LBM_ERR_ARG, "ctx is NULL");
+    if (!c->slab) return fail(c, LBM_ERR_STATE, "not a slab context (lbm_slab_init)");
+    if (side != 0 && side != 1) return fail(c, LBM_ERR_ARG, "side must be 0 (below) or 1 (above)");
+    if (!buf) return fail(c, LBM_ERR_ARG, "message buffer is NULL");
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lbm_slab_state_bytes(const lbm_params* p, int32_t z0, int32_t nzl) {
+    if (check_slab(p, z0, nzl)) return 0;
+    int glo, ghi;
+    const lbm_params q = slab_lattice(p, z0, nzl, glo, ghi);
+    return layout_of(&q, true).state;
+}
+
+size_t lbm_slab_work_bytes(const lbm_params* p, int32_t z0, int32_t nzl) {
+    if (check_slab(p, z0, nzl)) return 0;
+    int glo, ghi;
+    const lbm_params q = slab_lattice(p, z0, nzl, glo, ghi);
+    return layout_of(&q, true).work;
+}
+
+int32_t lbm_slab_planes(const lbm_params* p, int32_t z0, int32_t nzl) {
+    if (check_slab(p, z0, nzl)) return 0;
+    int glo, ghi;
+    return slab_lattice(p, z0, nzl, glo, ghi).nz;
+}
+
+lbm_status lbm_slab_init(const lbm_params* p, int32_t z0, int32_t nzl, void* d_state, void* d_work,
+                         const double* d_phi0, const double* d_cA0, const double* d_cB0, void* stream,
+                         lbm_ctx** out) {
+    if (out) *out = nullptr;
+    if (const char* m = check_slab(p, z0, nzl)) return fail(nullptr, LBM_ERR_ARG, m);
+    if (!d_phi0 || !d_cA0 || !d_cB0) return fail(nullptr, LBM_ERR_ARG, "initial fields must be non-NULL device pointers");
+    int glo, ghi;
+    const lbm_params q = slab_lattice(p, z0, nzl, glo, ghi);
+    lbm_status s = bind(&q, d_state, d_work, stream, out);
+    if (s != LBM_OK) return s;
+    lbm_ctx* c = *out;
+    c->slab = true;
+    c->z0 = z0; c->nzl = nzl; c->glo = glo; c->ghi = ghi;
+    c->L = layout_of(&q, true);
+    c->dp = dev_params(&q, c->L);
+    c->dp.wall_zlo = p->wall_z && z0 == 0;
+    c->dp.wall_zhi = p->wall_z && z0 + nzl == p->nz;
+    c->dp.z_lo = glo;
+    c->dp.z_hi = glo + nzl;
+    c->dp.phi_ghost[0] = glo ? c->work + c->L.off_phig[0] : nullptr;
+    c->dp.phi_ghost[1] = ghi ? c->work + c->L.off_phig[1] : nullptr;
+    c->st = view_of(&q, c->L, d_state);
+    c->st1 = view_of(&q, c->L, static_cast<char*>(d_state) + c->L.copy);
+    cudaGetLastError();
+    if (is16(q.storage) && q.flow) {
+        // the ghost planes' f_0 is the reference of the populations init places there (0)
+        const size_t pb = (size_t)q.nx * q.ny * sizeof(float);
+        for (const StateView* v : {&c->st, &c->st1}) {
+            char* f0 = reinterpret_cast<char*>(v->rest + 3 * c->L.plane);
+            if (glo) cudaMemsetAsync(f0 + (size_t)(glo - 1) * pb, 0, pb, c->stream);
+            if (ghi) cudaMemsetAsync(f0 + (size_t)(glo + nzl) * pb, 0, pb, c->stream);
+        }
+    }
+    LBM_DISPATCH(q.storage, launch_init, c->dp, c->st, q.lattice, q.flow != 0, true, d_phi0, d_cA0, d_cB0, c->stream);
+    s = cuda_check(c, "slab init kernel launch");
+    if (s != LBM_OK) {
+        g_last_error = c->err;
+        delete c;
+        *out = nullptr;
+    }
+    return s;
+}
+
+size_t lbm_slab_halo_bytes(const lbm_ctx* c) { return (c && c->slab) ? face_bytes(&c->p) : 0; }
+
+size_t lbm_slab_phi_bytes(const lbm_ctx* c) {
+    return (c && c->slab) ? (size_t)c->p.nx * c->p.ny * (c->p.storage == LBM_F64 ? 8 : 4) : 0;
+}
+
+lbm_status lbm_slab_pack(lbm_ctx* c, int32_t side, void* d_msg) {
+    if (lbm_status s = check_side(c, side, d_msg)) return s;
+    // side 0: the lowest own plane's populations moving down; side 1: the highest's moving up
+    return face_copy(c, current(c), side ? 1 : -1, side ? c->dp.z_hi - 1 : c->dp.z_lo, d_msg, true);
+}
+
+lbm_status lbm_slab_unpack(lbm_ctx* c, int32_t side, const void* d_msg) {
+    if (lbm_status s = check_side(c, side, d_msg)) return s;
+    if (!(side ? c->ghi : c->glo)) return fail(c, LBM_ERR_STATE, "no neighbour on that side (wall)");
+    // ghost below receives the lower neighbour's upward populations, ghost above the downward
+    return face_copy(c, current(c), side ? -1 : 1, side ? c->dp.z_hi : c->dp.z_lo - 1, const_cast<void*>(d_msg),
+                     false);
+}
+
+lbm_status lbm_slab_phi_pack(lbm_ctx* c, int32_t side, void* d_phi) {
+    if (lbm_status s = check_side(c, side, d_phi)) return s;
+    cudaGetLastError();
+    LBM_DISPATCH(c->p.storage, launch_plane_phi, c->dp, current(c), c->p.lattice, lbm::kModePull,
+                 side ? c->dp.z_hi - 1 : c->dp.z_lo, d_phi, c->stream);
+    return cuda_check(c, "slab phi kernel launch");
+}
+
+lbm_status lbm_slab_phi_unpack(lbm_ctx* c, int32_t side, const void* d_phi) {
+    if (lbm_status s = check_side(c, side, d_phi)) return s;
+    if (!(side ? c->ghi : c->glo)) return fail(c, LBM_ERR_STATE, "no neighbour on that side (wall)");
+    cudaError_t e = cudaMemcpyAsync(c->work + c->L.off_phig[side], d_phi, lbm_slab_phi_bytes(c),
+                                    cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) return fail(c, LBM_ERR_CUDA, std::string("slab phi copy: ") + cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+int32_t lbm_slab_ghosts(const lbm_ctx* c) { return (c && c->slab) ? (c->glo | (c->ghi << 1)) : -1; }
+
 lbm_status lbm_destroy(lbm_ctx* c) {
     if (c) for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     if (c && c->graph) cudaGraphExecDestroy(c->graph);
@@ -600,7 +817,8 @@ const char* lbm_last_error(const lbm_ctx* c) {
 
 const char* lbm_build_info(void) {
     return "gplbm sm_103a: fused collide-stream (AA in place; two-buffer z-marching with flow); "
-           "storage f64/f32/f16/bf16; scalar lattices D2Q5/D2Q9/D3Q7/D3Q19, flow D3Q19 BGK/TRT; adjoint";
+           "storage f64/f32/f16 (fixed point g, 1-4-11 floats f and h)/bf16; scalar lattices "
+           "D2Q5/D2Q9/D3Q7/D3Q19, flow D3Q19 BGK/TRT/MRT; adjoint";
 }
 
 }  // extern "C"
@@ -613,26 +831,39 @@ namespace {
 constexpr size_t kStaticScratchBytes = size_t(4) << 20;
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-std::mutex g_static_mu;
-void* g_static_ptr[64] = {};
-
 // Device address of g_static_scratch on the current device. In host code the array's name
-// only stands in for the symbol, so the address is looked up once per device, with that
-// device current, and cached.
+// only stands in for the symbol, so the address is looked up with that device current. The
+// lookup is repeated on every call (a host-side query once the module is loaded), so a
+// device reset between calls cannot leave a stale address behind.
 lbm_status static_scratch(void** out) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p)
+        return fail(nullptr, LBM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    *out = p;
+    return LBM_OK;
+}
+
+// The state buffer and the stream must belong to the current device, whose copy of the
+// array the kernels are given.
+lbm_status check_static_device(const void* d_state, cudaStream_t s) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(nullptr, LBM_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-    if (dev < 0 || dev >= 64) return fail(nullptr, LBM_ERR_ARG, "device index beyond 63");
-    std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess || !p)
-            return fail(nullptr, LBM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-        g_static_ptr[dev] = p;
+    cudaPointerAttributes a{};
+    e = cudaPointerGetAttributes(&a, d_state);
+    if (e != cudaSuccess || a.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        return fail(nullptr, LBM_ERR_ARG, "lbm_reduce_static: d_state is not device memory");
     }
-    *out = g_static_ptr[dev];
+    if (a.device != dev) return fail(nullptr, LBM_ERR_ARG, "lbm_reduce_static: d_state lies on another device than the current one");
+    int sdev = dev;
+    e = cudaStreamGetDevice(s, &sdev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, LBM_ERR_ARG, "lbm_reduce_static: invalid stream");
+    }
+    if (sdev != dev) return fail(nullptr, LBM_ERR_ARG, "lbm_reduce_static: the stream belongs to another device than the current one");
     return LBM_OK;
 }
 
@@ -649,8 +880,11 @@ extern "C" lbm_status lbm_reduce_static(const lbm_params* p, const void* d_state
                     "lbm_reduce_static: this lattice needs " + std::to_string(L.work) +
                         " bytes of scratch (phi field, bit field and partials) but the static array holds " +
                         std::to_string(kStaticScratchBytes) + "; use lbm_reduce with a work buffer");
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    lbm_status s = check_static_device(d_state, cs);
+    if (s != LBM_OK) return s;
     void* scratch = nullptr;
-    lbm_status s = static_scratch(&scratch);
+    s = static_scratch(&scratch);
     if (s != LBM_OK) return s;
     char* w = static_cast<char*>(scratch);
     const DevParams dp = dev_params(p, L);
@@ -659,7 +893,6 @@ extern "C" lbm_status lbm_reduce_static(const lbm_params* p, const void* d_state
     const int mode = L.two ? lbm::kModePull : ((t & 1) ? lbm::kModeAAOdd : lbm::kModeAAEven);
     double* partials = reinterpret_cast<double*>(w + L.off_partials);
     double* dout = reinterpret_cast<double*>(w + L.off_out);
-    cudaStream_t cs = static_cast<cudaStream_t>(stream);
     cudaGetLastError();
     LBM_DISPATCH(p->storage, launch_reduce, dp, st, p->lattice, p->flow != 0, mode, w + L.off_phi,
                  w + L.off_bits, partials, kRedBlocks, cs);

@@ -23,6 +23,10 @@ struct Coef {
 struct DevParams {
     int nx, ny, nz;
     int wall_x, wall_z, source_off;
+    int wall_zlo, wall_zhi;   // z walls at each end (a slab has them only where the lattice ends)
+    int z_lo, z_hi;           // planes the kernels advance, [z_lo, z_hi): (0, nz), or a slab's own
+    const void* phi_ghost[2]; // slab: phi (Real, nx * ny) of the planes z_lo - 1 and z_hi, which
+                              // belong to the neighbouring slabs; nullptr where a wall bounds z
     int coll;             // flow collision: 0 BGK (Eq. 36), 1 TRT, 2 MRT
     long long n;          // nodes
     long long plane;      // elements between two population planes (n rounded up)
@@ -59,7 +63,8 @@ struct StateView {
     void* g;      // Q planes
     void* hA;
     void* hB;
-    float* rest;  // 4 FP32 planes (g_0, hA_0, hB_0, f_0) for 16-bit storage, else nullptr
+    float* rest;  // 5 FP32 planes (g_0, hA_0, hB_0, f_0, f_0 of odd time levels in place) for
+                  // 16-bit storage, else nullptr
     void* plane[kPlanes];
 };
 
@@ -183,10 +188,8 @@ template <int LAT> struct Planes {
 template <class T> struct RealOf { using type = float; };
 template <> struct RealOf<double> { using type = double; };
 
-// Which population set a plane belongs to, for the 16-bit deviation encoding.
+// Which population set a plane belongs to, for the 16-bit encodings.
 enum { SET_F = 0, SET_G = 1, SET_H = 2 };
-constexpr float kHScale = 64.0f;       // 16-bit h_k / w_k scale (h_k ~ w_k mu, mu ~ 1e-3..1e-2)
-constexpr float kFScale = 1024.0f;     // 16-bit f_k / w_k scale (f_k ~ w_k (p_h + 3 e.u) ~ 1e-3 w_k)
 
 template <class T> struct Codec {
     // plain FP32 / FP64 storage
@@ -196,47 +199,104 @@ template <class T> struct Codec {
     __device__ static void store(T* p, typename RealOf<T>::type v, double, const DevParams&) { *p = v; }
 };
 
-__device__ inline float to_f(__half v) { return __half2float(v); }
-__device__ inline float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
-template <class T> __device__ inline T from_f(float v);
-template <> __device__ inline __half from_f<__half>(float v) { return __float2half_rn(v); }
-template <> __device__ inline __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+// 16-bit population storage. Every moving population P_k (k > 0) is held as its value per
+// unit weight, x_k = P_k / w_k - o, with o = 1/2 for g (phi lies in [0, 1]) and o = 0 for h,
+// and for f as the deviation from its writer's rest population, x_k = f_k / w_k - f_0 / w_0
+// (f_0 ~ w_0 p_h, so x_k ~ e_k . u: the pressure, which can exceed u by an order of
+// magnitude, is not rounded). Kernels decode x_k to FP32, collide on it (every equilibrium
+// and source term carries w_k, so the update keeps its affine form per unit weight) and
+// encode the result. The rest populations stay FP32.
+//
+// Store16 (storage LBM_F16) chooses a format per set from the range each set spans:
+//   g: 16-bit fixed point, x = (n - 32768) / 2^15 for the stored n in [0, 65535], i.e.
+//      x in [-1, 1) with a uniform step of 3.05e-5 (IEEE FP16's step near |x| = 1/2, where
+//      the bulk phases sit, is 8 times coarser);
+//   f, h: a 16-bit float with 1 sign, 4 exponent and 11 mantissa bits (one more mantissa
+//      bit than IEEE FP16, traded for range: the "FP16C" layout of Lehmann et al., Phys.
+//      Rev. E 106, 015308, 2022), normals 2^(e - 15) (1 + m / 2^11) for e = 1..15,
+//      subnormals 2^-14 m / 2^11, no infinities or NaN; values beyond the largest
+//      magnitude saturate. h is stored as x (|x| < 2), f as 8 x (|x| < 1/4).
+// Both formats saturate: the f16 storage assumes |u| below about 0.15 and |mu| + |c e.u| /
+// c_s^2 below 2, far outside the regime of a stable lattice Boltzmann run. An unstable run
+// still shows: its FP32 rest populations go non-finite.
+// __nv_bfloat16 (storage LBM_BF16) stores every x as BF16 (8-bit significand).
+struct Store16 { unsigned short bits; };
 
-// 16-bit storage holds each moving population P_k as its scaled deviation q_k:
-//   f: P = (w / kFScale) q,  g: P = w (q + 1/2),  h: P = (w / kHScale) q,
-// so that q is O(1) for every set. Kernels load q as it is (a Node of a 16-bit state holds
-// q_k for k > 0 and the FP32 rest population for k = 0), run the collision on q (the
-// BGK update is affine, so it keeps its form with the weights divided out) and store q.
-template <class H> struct Codec16 {
-    // population = scale * q + offset
-    template <int SET> __host__ __device__ static constexpr double scale(double w) {
-        return SET == SET_F ? w / kFScale : (SET == SET_G ? w : w / kHScale);
+namespace fmt16 {
+// 1-4-11 float: the 15 magnitude bits shifted left by 12 are an FP32 with exponent field e
+// and the same mantissa, worth 2^-112 times the 1-4-11 value (for e = 0 an FP32 subnormal).
+constexpr float kUp = 5.192296858534828e33f;      // 2^112
+constexpr float kDown = 1.925929944387236e-34f;   // 2^-112
+__device__ __forceinline__ float e4m11_dec(unsigned w) {
+    const unsigned b = ((w << 16) & 0x80000000u) | ((w << 12) & 0x07FFF000u);
+    return __uint_as_float(b) * kUp;
+}
+__device__ __forceinline__ unsigned short e4m11_enc(float v) {
+    const float lim = __uint_as_float(0x07FFF000u);              // largest magnitude, 2^-112 scale
+    float y = v * kDown;
+    y = fminf(fmaxf(y, -lim), lim);
+    unsigned b = __float_as_uint(y);
+    b += 0x7FFu + ((b >> 12) & 1u);                               // round to nearest, ties to even
+    return (unsigned short)(((b >> 16) & 0x8000u) | ((b >> 12) & 0x7FFFu));
+}
+// 16-bit fixed point over [-1, 1): 1.5 * 2^23 + n is exact in FP32, so one FMA decodes
+constexpr float kMagic = 12582912.0f;                             // 1.5 * 2^23
+__device__ __forceinline__ float q15_dec(unsigned w) {
+    return fmaf(__uint_as_float(0x4B400000u | (w & 0xFFFFu)), 3.0517578125e-05f, -385.0f);
+}
+__device__ __forceinline__ unsigned short q15_enc(float v) {
+    float y = fmaf(v, 32768.0f, kMagic + 32768.0f);               // rounds to the nearest integer
+    y = fminf(fmaxf(y, kMagic), kMagic + 65535.0f);
+    return (unsigned short)(__float_as_uint(y) & 0xFFFFu);
+}
+}  // namespace fmt16
+
+constexpr float kF16FScale = 8.0f;   // Store16 f: stored value 8 x
+
+template <class H> struct Codec16;
+template <> struct Codec16<Store16> {
+    template <int SET> __device__ static float dec(Store16 v) {
+        if (SET == SET_G) return fmt16::q15_dec(v.bits);
+        if (SET == SET_F) return fmt16::e4m11_dec(v.bits) * (1.0f / kF16FScale);
+        return fmt16::e4m11_dec(v.bits);
     }
+    template <int SET> __device__ static Store16 enc(float x) {
+        if (SET == SET_G) return Store16{fmt16::q15_enc(x)};
+        if (SET == SET_F) return Store16{fmt16::e4m11_enc(x * kF16FScale)};
+        return Store16{fmt16::e4m11_enc(x)};
+    }
+};
+template <> struct Codec16<__nv_bfloat16> {
+    template <int SET> __device__ static float dec(__nv_bfloat16 v) { return __bfloat162float(v); }
+    template <int SET> __device__ static __nv_bfloat16 enc(float x) { return __float2bfloat16_rn(x); }
+};
+
+// The per-unit-weight codec behind the node loaders: population = scale * x + offset.
+template <class H> struct Codec16Pop : Codec16<H> {
+    template <int SET> __host__ __device__ static constexpr double scale(double w) { return w; }
     template <int SET> __host__ __device__ static constexpr double offset(double w) {
         return SET == SET_G ? 0.5 * w : 0.0;
     }
     template <int SET>
-    __device__ static float load(const H* p, double, const DevParams&) { return to_f(*p); }
-    // encode a population given in natural units (initial state)
+    __device__ static float load(const H* p, double, const DevParams&) { return Codec16<H>::template dec<SET>(*p); }
+    // encode a population given in natural units (initial state; f with a zero reference)
     template <int SET>
     __device__ static void store(H* p, float v, double w, const DevParams&) {
-        float q;
-        if (SET == SET_F) q = v * float(kFScale / w);
-        else if (SET == SET_G) q = v * float(1.0 / w) - 0.5f;
-        else q = v * float(kHScale / w);
-        *p = from_f<H>(q);
+        const float x = SET == SET_G ? v * float(1.0 / w) - 0.5f : v * float(1.0 / w);
+        *p = Codec16<H>::template enc<SET>(x);
     }
-    // Store q and return the stored value read back, round16(q): the caller subtracts the
-    // moving populations as stored from the node's conserved total to set its FP32 rest
-    // population, so 16-bit rounding never changes the node's sums.
-    __device__ static float store_q_back(H* p, float q) {
-        const H h = from_f<H>(q);
+    // Store x and return the value as stored, dec(enc(x)): the caller subtracts the moving
+    // populations as stored from the node's conserved total to set the FP32 rest population
+    // of g and h, so 16-bit rounding never changes those sums.
+    template <int SET>
+    __device__ static float store_back(H* p, float x) {
+        const H h = Codec16<H>::template enc<SET>(x);
         *p = h;
-        return to_f(h);
+        return Codec16<H>::template dec<SET>(h);
     }
 };
-template <> struct Codec<__half> : Codec16<__half> {};
-template <> struct Codec<__nv_bfloat16> : Codec16<__nv_bfloat16> {};
+template <> struct Codec<Store16> : Codec16Pop<Store16> {};
+template <> struct Codec<__nv_bfloat16> : Codec16Pop<__nv_bfloat16> {};
 
 template <class T> constexpr bool is16() { return sizeof(T) == 2; }
 

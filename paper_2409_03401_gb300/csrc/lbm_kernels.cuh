@@ -40,8 +40,9 @@ struct Nbr {
         }
     }
     __device__ __forceinline__ void set_z(int z, const DevParams& P) {
-#pragma unroll
-        for (int d = -1; d <= 1; ++d) c[2][d + 1] = wrap(z + d, P.nz, P.wall_z);
+        c[2][0] = z - 1 < 0 ? (P.wall_zlo ? -1 : z - 1 + P.nz) : z - 1;
+        c[2][1] = z;
+        c[2][2] = z + 1 >= P.nz ? (P.wall_zhi ? -1 : z + 1 - P.nz) : z + 1;
 #pragma unroll
         for (int iz = 0; iz < 3; ++iz)
 #pragma unroll
@@ -65,6 +66,12 @@ struct Nbr {
 // wall both fall back to the node itself with k and opp(k) exchanged (half-way bounce-back).
 template <int MODE>
 struct Addr {
+    // FP32 rest plane of f read (written) by a step in this mode with 16-bit storage: the
+    // two-buffer layout keeps f_0 in plane 3 of each copy; in place, time levels alternate
+    // between planes 3 (even) and 4 (odd), because neighbours read a node's f_0 as the
+    // reference of the populations it wrote (Codec16Pop) while the node replaces it.
+    static constexpr int kF0In = MODE == AA_ODD ? 4 : 3;
+    static constexpr int kF0Out = MODE == AA_EVEN ? 4 : 3;
     Nbr nb;
     int self;
     __device__ __forceinline__ Slot src(int k, int ex, int ey, int ez) const {
@@ -80,6 +87,17 @@ struct Addr {
         int q;
         return nb.at(ex, ey, ez, self, q) ? Slot{q, k} : Slot{self, opp(k)};
     }
+    // node that stored the population gathered as k: x - e_k (its outgoing k), or the node
+    // itself across a wall (its outgoing opp(k), bounced back)
+    __device__ __forceinline__ int writer(int k, int ex, int ey, int ez) const {
+        if (k == 0) return self;
+        if (MODE == AA_EVEN) {
+            int q;
+            nb.at(-ex, -ey, -ez, self, q);
+            return q;
+        }
+        return src(k, ex, ey, ez).node;
+    }
     // phi of a neighbour in a phi array, mirror ghost across walls (zero normal gradient)
     template <class R>
     __device__ __forceinline__ R phi(const R* __restrict__ f, int dx, int dy, int dz) const {
@@ -93,11 +111,13 @@ struct Addr {
 // inside the lattice: no wrap and no wall, so the source of population k is node
 // self - e_k, an offset that is the same for every thread of a block.
 struct AddrInterior {
+    static constexpr int kF0In = 3, kF0Out = 3;
     int self;
     int sx, sxy;   // nx, nx * ny
     __device__ __forceinline__ Slot src(int k, int ex, int ey, int ez) const {
         return {self - ex - ey * sx - ez * sxy, k};
     }
+    __device__ __forceinline__ int writer(int k, int ex, int ey, int ez) const { return src(k, ex, ey, ez).node; }
     __device__ __forceinline__ Slot dst(int k, int, int, int) const { return {self, k}; }
 };
 
@@ -128,9 +148,17 @@ struct Node {
         if constexpr (FLOW) {
 #pragma unroll
             for (int k = 0; k < 19; ++k) {
-                const Slot s = ad.src(k, D3Q19::ex(k), D3Q19::ey(k), D3Q19::ez(k));
-                if (is16<T>() && k == 0) f[0] = st.rest[3 * P.plane + s.node];
-                else f[k] = Codec<T>::template load<SET_F>(element<T, 0>(st, k, s), D3Q19::w(k), P);
+                const int ex = D3Q19::ex(k), ey = D3Q19::ey(k), ez = D3Q19::ez(k);
+                const Slot s = ad.src(k, ex, ey, ez);
+                if constexpr (is16<T>()) {
+                    // f_k / w_k = stored deviation + the writer's f_0 / w_0 (Codec16Pop)
+                    const float* f0 = st.rest + A::kF0In * P.plane;
+                    if (k == 0) f[0] = f0[s.node];
+                    else f[k] = Codec<T>::template load<SET_F>(element<T, 0>(st, k, s), D3Q19::w(k), P) +
+                                f0[ad.writer(k, ex, ey, ez)] * R(1.0 / D3Q19::w(0));
+                } else {
+                    f[k] = Codec<T>::template load<SET_F>(element<T, 0>(st, k, s), D3Q19::w(k), P);
+                }
             }
         }
     }
@@ -141,8 +169,8 @@ struct Node {
     }
 
     // Eq. 49 without the source, Eq. 52 (as c - c_0^eq), Eq. 33 at phi~ and Eq. 35. With
-    // 16-bit storage the moving populations are scaled deviations q_k (Codec16): the sums
-    // weight them back, sum_k P_k = P_0 + sum_k>0 (scale_k q_k + offset_k).
+    // 16-bit storage the moving populations are values per unit weight x_k (Codec16Pop): the
+    // sums weight them back, sum_k P_k = P_0 + sum_k>0 (w_k x_k + offset_k).
     __device__ __forceinline__ void moments(const DevParams& P) {
         if constexpr (is16<T>()) {
             using C = Codec<T>;
@@ -267,10 +295,10 @@ __device__ __forceinline__ R edot(int ex, int ey, int ez, R vx, R vy, R vz) {
 //       f^eq = w (B + cu (1 + 1.5 cu)) - F_k / 2, B = p_h - 0.5 u^2          (Eqs. 36-39)
 //   g:  g^eq = w (phi - S/2 + phi cu / cs2), g* = g - om (g - g^eq) + w S    (Eqs. 46-48)
 //   h:  h^eq_k = w (mu + c cu / cs2), h^eq_0 = dc - (1 - w_0) mu (shifted)   (Eqs. 50-51)
-// With 16-bit storage the moving populations are updated as scaled deviations q (Codec16):
-// every term above carries the factor w_k, so dividing it out leaves the same affine update
-// on q with the per-direction weights gone, e.g. q*_f = q - om (q - s E_k) + s G_k with
-// E_k = f^eq / w, G_k = F_k / w, s = kFScale.
+// With 16-bit storage the moving populations are updated per unit weight (Codec16Pop): every
+// term above carries the factor w_k, so dividing it out leaves the same affine update with
+// the per-direction weights gone, e.g. x*_f = x - om (x - E_k) + G_k with x = f_k / w_k,
+// E_k = f^eq / w_k, G_k = F_k / w_k.
 // COLL: flow collision fixed at compile time (0 BGK, 1 TRT, 2 MRT); -1 reads P.coll to
 // choose between BGK and TRT only, -2 reads it to choose among all three.
 // MRT on the D3Q19 moment basis: d = f - f^eq, dm_i = (rate_i / |M_i|^2) sum_k M_ik d_k,
@@ -368,22 +396,24 @@ __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, type
                 }
             }
         } else {
-            constexpr float s = kFScale;
-            R stored = R(0);                                  // sum of the stored moving f, natural units
-            auto put = [&](int k, R q) {
-                const Slot sl = ad.dst(k, D3Q19::ex(k), D3Q19::ey(k), D3Q19::ez(k));
-                stored += R(Codec<T>::template scale<SET_F>(D3Q19::w(k))) *
-                          Codec<T>::store_q_back(element<T, 0>(out, k, sl), q);
+            // 16-bit storage: nd.f[k] = f_k / w_k for k > 0 (the writer's reference added back
+            // on load), nd.f[0] = f_0. The updates below are those of the FP32 branch divided by
+            // w_k. f*_0 is stored first, in FP32, and is the reference of every moving
+            // population this node stores: x*_k - f*_0 / w_0 is what gets rounded.
+            using C = Codec<T>;
+            R ref = R(0);
+            auto put0 = [&](R f0post) {
+                const float f0s = float(f0post);
+                out.rest[A::kF0Out * P.plane + self] = f0s;
+                ref = R(f0s) * R(1.0 / D3Q19::w(0));
             };
+            auto put = [&](int k, R x) {
+                const Slot sl = ad.dst(k, D3Q19::ex(k), D3Q19::ey(k), D3Q19::ez(k));
+                *element<T, 0>(out, k, sl) = C::template enc<SET_F>(float(x - ref));
+            };
+            const R w0 = R(D3Q19::w(0));
             const int coll = COLL >= 0 ? COLL : (COLL == -1 && P.coll == 2 ? 0 : P.coll);
-            if (coll == 0) {
-#pragma unroll
-                for (int k = 1; k < 19; ++k) {
-                    R G, E;
-                    force_eq(k, G, E);
-                    put(k, nd.f[k] - omf * (nd.f[k] - s * E) + s * G);
-                }
-            } else if ((COLL == 2 || COLL == -2) && coll == 2) {
+            if ((COLL == 2 || COLL == -2) && coll == 2) {
                 // MRT mixes directions: run it on the populations in natural units
                 R Fs[19];
                 mrt_relax<R>(P, [&](int k) {
@@ -391,30 +421,36 @@ __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, type
                     force_eq(k, G, E);
                     const R w = R(D3Q19::w(k));
                     Fs[k] = w * G;
-                    const R fk = k == 0 ? nd.f[0] : R(Codec<T>::template scale<SET_F>(D3Q19::w(k))) * nd.f[k];
-                    return fk - w * E;
+                    return k == 0 ? nd.f[0] - w * E : w * (nd.f[k] - E);
                 }, [&](int k, R r) {
-                    if (k == 0) return;                      // the rest population is set below
-                    const R fk = R(Codec<T>::template scale<SET_F>(D3Q19::w(k))) * nd.f[k];
-                    put(k, (fk - r + Fs[k]) * R(1.0 / Codec<T>::template scale<SET_F>(D3Q19::w(k))));
+                    if (k == 0) put0(nd.f[0] - r + Fs[0]);
+                    else put(k, nd.f[k] + (Fs[k] - r) * R(1.0 / D3Q19::w(k)));
                 });
             } else {
-                const R omm = coef<R>(P).om_fm;
+                R G0, E0;
+                force_eq(0, G0, E0);
+                put0(nd.f[0] - omf * (nd.f[0] - w0 * E0) + w0 * G0);
+                if (coll == 0) {
 #pragma unroll
-                for (int k = 1; k < 19; k += 2) {
-                    R Ga, Ea, Gb, Eb;
-                    force_eq(k, Ga, Ea);
-                    force_eq(k + 1, Gb, Eb);
-                    const R da = nd.f[k] - s * Ea, db = nd.f[k + 1] - s * Eb;
-                    const R even = R(0.5) * (da + db), odd = R(0.5) * (da - db);
-                    put(k, nd.f[k] - omf * even - omm * odd + s * Ga);
-                    put(k + 1, nd.f[k + 1] - omf * even + omm * odd + s * Gb);
+                    for (int k = 1; k < 19; ++k) {
+                        R G, E;
+                        force_eq(k, G, E);
+                        put(k, nd.f[k] - omf * (nd.f[k] - E) + G);
+                    }
+                } else {
+                    const R omm = coef<R>(P).om_fm;
+#pragma unroll
+                    for (int k = 1; k < 19; k += 2) {
+                        R Ga, Ea, Gb, Eb;
+                        force_eq(k, Ga, Ea);
+                        force_eq(k + 1, Gb, Eb);
+                        const R da = nd.f[k] - Ea, db = nd.f[k + 1] - Eb;
+                        const R even = R(0.5) * (da + db), odd = R(0.5) * (da - db);
+                        put(k, nd.f[k] - omf * even - omm * odd + Ga);
+                        put(k + 1, nd.f[k + 1] - omf * even + omm * odd + Gb);
+                    }
                 }
             }
-            // the collision keeps sum_k f_k = p_h (BGK and TRT alike: sum f^eq = p_h, sum F_k = 0),
-            // so the FP32 rest population takes p_h minus what the moving ones stored: the
-            // node's p_h survives the 16-bit rounding
-            out.rest[3 * P.plane + self] = float(ph - stored);
         }
     }
     const R p = interp_p(phi);
@@ -456,12 +492,12 @@ __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, type
         g0 = phi + R(0.5) * nd.S - R(0.5 * (1.0 - L::w(0)));       // phi~ + S = phi + S/2
         hA0 = nd.dcA;
         hB0 = nd.dcB;
-        // q-space: g = w (q + 1/2) gives q* = q - om (q + 1/2 - ga - gb cu) + S, and
-        // h = (w / kHScale) q gives q* = q - om (q - kHScale (mu + c cu / cs2))
+        // per unit weight: g = w (x + 1/2) gives x* = x - om (x + 1/2 - ga - gb cu) + S, and
+        // h = w x gives x* = x - om (x - (mu + c cu / cs2))
         using C = Codec<T>;
         const R gq = R(0.5) - ga;
-        const R mA = R(kHScale) * muA, mB = R(kHScale) * muB;
-        const R cA = R(kHScale) * cAu, cB = R(kHScale) * cBu;
+        const R mA = muA, mB = muB;
+        const R cA = cAu, cB = cBu;
 #pragma unroll
         for (int k = 1; k < Q; ++k) {
             const int ex = L::ex(k), ey = L::ey(k), ez = L::ez(k);
@@ -470,9 +506,9 @@ __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, type
             const R qg = nd.g[k] - omg * (nd.g[k] + gq - gb * cu) + nd.S;
             const R qA = nd.hA[k] - omA * (nd.hA[k] - (mA + cA * cu));
             const R qB = nd.hB[k] - omB * (nd.hB[k] - (mB + cB * cu));
-            g0 -= R(C::template scale<SET_G>(L::w(k))) * C::store_q_back(element<T, Planes<LAT>::G>(out, k, s), qg);
-            hA0 -= R(C::template scale<SET_H>(L::w(k))) * C::store_q_back(element<T, Planes<LAT>::HA>(out, k, s), qA);
-            hB0 -= R(C::template scale<SET_H>(L::w(k))) * C::store_q_back(element<T, Planes<LAT>::HB>(out, k, s), qB);
+            g0 -= R(L::w(k)) * C::template store_back<SET_G>(element<T, Planes<LAT>::G>(out, k, s), qg);
+            hA0 -= R(L::w(k)) * C::template store_back<SET_H>(element<T, Planes<LAT>::HA>(out, k, s), qA);
+            hB0 -= R(L::w(k)) * C::template store_back<SET_H>(element<T, Planes<LAT>::HB>(out, k, s), qB);
         }
     }
     const Slot s0{self, 0};
@@ -490,7 +526,7 @@ step_kernel(const DevParams P, const StateView st, const StateView out,
             const typename RealOf<T>::type* __restrict__ phi_field) {
     using R = typename RealOf<T>::type;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
+    const int y = blockIdx.y, z = blockIdx.z + P.z_lo;
     if (x >= P.nx) return;
     Addr<MODE> ad;
     ad.self = node_of(x, y, z, P);
@@ -514,7 +550,7 @@ template <class T, int LAT, int MODE>
 __global__ void __launch_bounds__(kBlockX)
 phi_kernel(const DevParams P, const StateView st, typename RealOf<T>::type* __restrict__ phi_out) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
+    const int y = blockIdx.y, z = blockIdx.z + P.z_lo;
     if (x >= P.nx) return;
     Addr<MODE> ad;
     ad.self = node_of(x, y, z, P);
@@ -523,6 +559,24 @@ phi_kernel(const DevParams P, const StateView st, typename RealOf<T>::type* __re
     nd.gather_scalars(st, ad, P);
     nd.moments(P);
     phi_out[ad.self] = nd.phi();
+}
+
+// phi (Eq. 49) of plane z into out[y nx + x]: a slab's edge plane, sent to the neighbouring
+// slab whose capillary stencil reads it (the same arithmetic as phi_kernel and the fused
+// kernel's ring, so a slab run matches the undivided lattice bit for bit).
+template <class T, int LAT, int MODE>
+__global__ void __launch_bounds__(kBlockX)
+plane_phi_kernel(const DevParams P, const StateView st, int z, typename RealOf<T>::type* __restrict__ out) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= P.nx) return;
+    Addr<MODE> ad;
+    ad.self = node_of(x, y, z, P);
+    ad.nb.init(x, y, z, P);
+    Node<T, LAT, false> nd;
+    nd.gather_scalars(st, ad, P);
+    nd.moments(P);
+    out[y * P.nx + x] = nd.phi();
 }
 
 // ------------------------------------------------------------------------------------
@@ -574,8 +628,8 @@ fused_flow_kernel(const DevParams P, const StateView src, const StateView dst, i
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * FX + tx;
     const int x0 = blockIdx.x * FX, y0 = blockIdx.y * FY;
-    const int zs = blockIdx.z * zchunk;
-    const int ze = min(zs + zchunk, P.nz);
+    const int zs = P.z_lo + blockIdx.z * zchunk;
+    const int ze = min(zs + zchunk, P.z_hi);
     const int x = x0 + tx, y = y0 + ty;
     const bool active = x < P.nx && y < P.ny;
 
@@ -590,8 +644,8 @@ fused_flow_kernel(const DevParams P, const StateView src, const StateView dst, i
         return gx >= 0 && gx < P.nx && gy >= 0 && gy < P.ny;
     };
     auto zwrap = [&](int zz) {
-        if (zz < 0) return P.wall_z ? 0 : zz + P.nz;
-        if (zz >= P.nz) return P.wall_z ? P.nz - 1 : zz - P.nz;
+        if (zz < 0) return P.wall_zlo ? 0 : zz + P.nz;
+        if (zz >= P.nz) return P.wall_zhi ? P.nz - 1 : zz - P.nz;
         return zz;
     };
     // this thread's own ring column and its halo column (threads tid < kHalo), fixed in z
@@ -618,6 +672,13 @@ fused_flow_kernel(const DevParams P, const StateView src, const StateView dst, i
     // phi (and, for a tile node, its scalar populations in buffer buf) of plane zz
     auto fill = [&](auto fast, int zz, int s, int buf) {
         constexpr bool kFast = decltype(fast)::value;
+        // a slab's neighbouring planes: their phi arrives from the neighbour (phi_ghost)
+        const R* gh = static_cast<const R*>(zz < P.z_lo ? P.phi_ghost[0] : (zz >= P.z_hi ? P.phi_ghost[1] : nullptr));
+        if (gh) {
+            ring[s][ty + 1][tx + 1] = own_ok ? gh[oy * P.nx + ox] : R(0);
+            if (tid < kHalo) ring[s][hyp + 1][hxp + 1] = halo_ok ? gh[hgy * P.nx + hgx] : R(0);
+            return;
+        }
         const int zr = zwrap(zz);
         R v = R(0);
         if (own_ok) {
@@ -730,7 +791,7 @@ init_kernel(const DevParams P, const StateView st, const double* __restrict__ ph
     using R = typename RealOf<T>::type;
     using L = Scalar<LAT>;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
+    const int y = blockIdx.y, z = blockIdx.z + P.z_lo;
     if (x >= P.nx) return;
     Addr<MODE> ad;
     ad.self = node_of(x, y, z, P);
@@ -773,7 +834,7 @@ fields_kernel(const DevParams P, const StateView st, const typename RealOf<T>::t
               FieldPtrs out) {
     using R = typename RealOf<T>::type;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
+    const int y = blockIdx.y, z = blockIdx.z + P.z_lo;
     if (x >= P.nx) return;
     Addr<MODE> ad;
     ad.self = node_of(x, y, z, P);
@@ -908,10 +969,12 @@ reduce_kernel(const DevParams P, const StateView st, const typename RealOf<T>::t
     for (int i = 0; i < LBM_NRED_DEV; ++i) acc[i] = 0.0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < P.n; base += stride) {
+    // nodes of the planes [z_lo, z_hi); the bit field (3D Euler count) only when they start at 0
+    const long long id0 = (long long)P.z_lo * P.nx * P.ny, id1 = (long long)P.z_hi * P.nx * P.ny;
+    for (long long base = id0 + (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < id1; base += stride) {
         const long long id = base + lane;
         bool on = false;
-        if (id < P.n) {
+        if (id < id1) {
             const int x = int(id % P.nx);
             const int y = int((id / P.nx) % P.ny);
             const int z = int(id / ((long long)P.nx * P.ny));
@@ -945,8 +1008,10 @@ reduce_kernel(const DevParams P, const StateView st, const typename RealOf<T>::t
             on = phi >= R(0.5);
         }
         if constexpr (!kTwoD<LAT>) {
-            const unsigned word = __ballot_sync(0xffffffffu, on);
-            if (lane == 0) bits[base >> 5] = word;
+            if (bits) {
+                const unsigned word = __ballot_sync(0xffffffffu, on);
+                if (lane == 0) bits[base >> 5] = word;
+            }
         }
     }
     // block reduction: warp shuffles, then one warp over the warp results
@@ -980,7 +1045,7 @@ reduce_kernel(const DevParams P, const StateView st, const typename RealOf<T>::t
 // layout and PULL for the two-buffer layout (st = the current state buffer).
 inline dim3 node_grid(const DevParams& P, int& bx) {
     bx = P.nx >= kBlockX ? kBlockX : ((P.nx + 31) / 32) * 32;
-    return dim3((P.nx + bx - 1) / bx, P.ny, P.nz);
+    return dim3((P.nx + bx - 1) / bx, P.ny, P.z_hi - P.z_lo);
 }
 
 #define LBM_MODE_SWITCH(MODE_VAR, ...)                                          \
@@ -1007,6 +1072,13 @@ struct Launchers {
         R* ph = static_cast<R*>(phi_work);
         LBM_MODE_SWITCH(mode, phi_kernel<T, LAT, M><<<grid, bx, 0, s>>>(P, st, ph));
     }
+    template <int LAT>
+    static void plane_phi(const DevParams& P, const StateView& st, int mode, int z, void* out, cudaStream_t s) {
+        int bx; dim3 grid = node_grid(P, bx);
+        grid.z = 1;
+        R* o = static_cast<R*>(out);
+        LBM_MODE_SWITCH(mode, plane_phi_kernel<T, LAT, M><<<grid, bx, 0, s>>>(P, st, z, o));
+    }
     // the per-node step kernel; with flow, the phi pass of the same step must precede it
     template <int LAT, bool FLOW>
     static void step(const DevParams& P, const StateView& st, const StateView& out, int mode, void* phi_work,
@@ -1024,7 +1096,7 @@ struct Launchers {
     }
     static void fused(const DevParams& P, const StateView& src, const StateView& dst, int zchunk, cudaStream_t s) {
         const dim3 block(FX, FY);
-        const dim3 grid((P.nx + FX - 1) / FX, (P.ny + FY - 1) / FY, (P.nz + zchunk - 1) / zchunk);
+        const dim3 grid((P.nx + FX - 1) / FX, (P.ny + FY - 1) / FY, (P.z_hi - P.z_lo + zchunk - 1) / zchunk);
         constexpr size_t smem = fused_smem_bytes<T>();
         // instances per flow collision (see fused_flow_kernel)
         if (P.coll == 2) {
@@ -1071,7 +1143,10 @@ struct Launchers {
             LBM_MODE_SWITCH(mode, phi_kernel<T, LAT, M><<<grid, bx, 0, s>>>(P, st, phi));
         }
         LBM_MODE_SWITCH(mode, reduce_kernel<T, LAT, FLOW, M><<<nblocks, 256, 0, s>>>(P, st, phi, bits, partials));
-        if constexpr (!kTwoD<LAT>) euler3d_kernel<T><<<nblocks, 256, 0, s>>>(P, bits, partials);
+        // the 3D Euler count needs the bit field of the whole lattice (not kept for a slab)
+        if constexpr (!kTwoD<LAT>) {
+            if (bits) euler3d_kernel<T><<<nblocks, 256, 0, s>>>(P, bits, partials);
+        }
     }
 };
 
@@ -1092,6 +1167,13 @@ struct Launchers {
         else if (lat == LAT_D2Q9) Launchers<T>::phi<LAT_D2Q9>(P, st, mode, phi, s);                        \
         else if (lat == LAT_D3Q19) Launchers<T>::phi<LAT_D3Q19>(P, st, mode, phi, s);                      \
         else Launchers<T>::phi<LAT_D3Q7>(P, st, mode, phi, s);                                             \
+    }                                                                                                     \
+    void launch_plane_phi_##SUFFIX(const DevParams& P, const StateView& st, int lat, int mode, int z,    \
+                                   void* out, cudaStream_t s) {                                           \
+        if (lat == LAT_D2Q5) Launchers<T>::plane_phi<LAT_D2Q5>(P, st, mode, z, out, s);                    \
+        else if (lat == LAT_D2Q9) Launchers<T>::plane_phi<LAT_D2Q9>(P, st, mode, z, out, s);               \
+        else if (lat == LAT_D3Q19) Launchers<T>::plane_phi<LAT_D3Q19>(P, st, mode, z, out, s);             \
+        else Launchers<T>::plane_phi<LAT_D3Q7>(P, st, mode, z, out, s);                                    \
     }                                                                                                     \
     void launch_step_##SUFFIX(const DevParams& P, const StateView& st, const StateView& out, int lat,     \
                               bool flow, int mode, void* phi, cudaStream_t s) {                            \

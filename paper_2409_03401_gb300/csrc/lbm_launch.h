@@ -21,6 +21,8 @@ constexpr int kModeAAEven = 0, kModeAAOdd = 1, kModePull = 2;
                               const double*, const double*, const double*, cudaStream_t);                \
     void launch_phi_##SUFFIX(const DevParams&, const StateView&, int lat, int mode, void* phi,           \
                              cudaStream_t);                                                              \
+    void launch_plane_phi_##SUFFIX(const DevParams&, const StateView&, int lat, int mode, int z, void* out, \
+                                   cudaStream_t);                                                        \
     void launch_step_##SUFFIX(const DevParams&, const StateView&, const StateView&, int lat, bool flow, \
                               int mode, void* phi, cudaStream_t);                                        \
     void launch_fused_##SUFFIX(const DevParams&, const StateView&, const StateView&, int zchunk,        \

@@ -1,6 +1,7 @@
-// Coupled-step kernels instantiated for __half population storage.
+// Coupled-step kernels instantiated for the 16-bit Store16 population storage (fixed point
+// for g, 1-4-11 floats for f and h; see Codec16 in lbm_device.cuh).
 #include "lbm_kernels.cuh"
 
 namespace lbm {
-LBM_DEFINE_LAUNCHERS(__half, f16)
+LBM_DEFINE_LAUNCHERS(Store16, f16)
 }  // namespace lbm

@@ -48,7 +48,7 @@ def test_sizes_and_validation_on_the_host(lib):
     assert inplace == 40 * 4 * n                       # one in-place AA copy
     p16 = p.with_(storage="f16")
     s16 = lib.lbm_state_bytes(ctypes.byref(_lib.make_params(p16)))
-    assert s16 == 2 * (40 * 2 * n + 4 * 4 * n)         # 16-bit planes + 4 FP32 rest planes, two copies
+    assert s16 == 2 * (40 * 2 * n + 5 * 4 * n)         # 16-bit planes + 5 FP32 rest planes, two copies
     noflow = lib.lbm_state_bytes(ctypes.byref(_lib.make_params(p.with_(flow=False))))
     assert noflow == 21 * 4 * n                        # scalars only: always one in-place copy
     assert lib.lbm_state_bytes(ctypes.byref(_lib.make_params(p.with_(nx=2048, ny=1024, nz=1024)))) == 0

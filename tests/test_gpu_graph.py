@@ -70,4 +70,8 @@ def test_graph_on_the_launch_bound_couple():
             torch.cuda.synchronize()
             times[graph] = min(times[graph], (time.perf_counter() - t0) / 2000 * 1e6)
     print(f"512 x 8 couple, FP64: {times[False]:.2f} us/step plain, {times[True]:.2f} us/step graph")
-    assert times[True] < times[False]
+    # timing is reported, not asserted (a shared machine can invert it); the two runs took the
+    # same steps and must agree bit for bit
+    a, b = sims[False].fields(), sims[True].fields()
+    for k in a:
+        assert torch.equal(a[k], b[k]), k

@@ -1,8 +1,8 @@
 """CUDA path vs the FP64 oracle, element by element, on seeded synthetic inputs.
 
 Tolerances (relative L-infinity, floors in tests/parity.py): FP64 storage 1e-12,
-FP32 storage 1e-5, FP16 storage 1e-3; BF16 storage (8-bit mantissa) is held to 1e-2
-and its measured gap is reported. Sizes span several thread blocks in x with a
+FP32 storage 1e-5, FP16 storage 1e-3 on every field; BF16 storage (8-bit significand) is
+a separate variant held to 1e-2 (phi, mu, c) and 3e-2 (p, u), its measured gap. Sizes span several thread blocks in x with a
 ragged tail (nx not a multiple of 128 or 32), both AA parities, walls and periodic
 wrap, and the degenerate one-node-thick directions.
 """
@@ -101,15 +101,12 @@ def test_flow_mrt(storage, inplace):
 
 @pytest.mark.parametrize("collision", ["TRT", "MRT"])
 def test_flow_collisions_fp16(collision):
-    # FP16 storage with TRT and MRT: phi, mu, c at the 16-bit bar of 1e-3; u and p at 3e-3,
-    # and 5e-3 with MRT, whose default m-moment rate 1.98 leaves the rounding noise of those
-    # third-order moments almost undamped (3.5e-3 measured on u_y)
+    # FP16 storage (fixed-point g, 1-4-11 floats for f and h, f relative to its writer's rest
+    # population) with TRT and MRT: every field at the 16-bit bar of 1e-3
     p, fields = configs.sedimentation(shape=(24, 24, 40), fraction=0.06, r=(4.0, 6.0), storage="f16")
     errs = compare(p.with_(collision=collision), fields(), 100)
     print(f"{collision} f16 errors after 100 steps: {errs}")
-    scal, tol_s, tol_u = BARS16["f16"]
-    _close({k: v for k, v in errs.items() if k in scal}, tol_s)
-    _close({k: v for k, v in errs.items() if k not in scal}, 5e-3 if collision == "MRT" else tol_u)
+    _close(errs, TOL["f16"])
 
 
 def test_flow_periodic_z_fp32():
@@ -153,12 +150,11 @@ def test_d2q5_fp32_and_walls():
     _close(compare(p, fields(), 300), TOL["f32"])
 
 
-# 16-bit storage (moving populations as FP16/BF16 deviations, rest populations FP32 with the
-# rounding residuals fed back). FP16 keeps phi, mu and c within 1e-3; the velocity and
-# pressure, small differences of ~1e-3 populations, reach ~2e-3 of max|u| while the flow is
-# young (measured 1.5e-3..2.2e-3 at 50 steps, below 1e-3 by 800). BF16 (8-bit mantissa) is
-# about ten times coarser. The bars below are those measured gaps, not the 1e-3 target.
-BARS16 = {"f16": ({"phi", "muA", "muB", "cA", "cB"}, 1e-3, 3e-3),
+# 16-bit storage (moving populations per unit weight in 16 bits, f relative to its writer's
+# FP32 rest population; rest populations FP32). LBM_F16 holds every field within the 16-bit
+# bar of 1e-3. LBM_BF16 (8-bit significand) is a separate variant that does not meet it: its
+# measured gap is printed and held to the bars below (an order of magnitude above 1e-3).
+BARS16 = {"f16": ({"phi", "muA", "muB", "cA", "cB"}, TOL["f16"], TOL["f16"]),
           "bf16": ({"phi", "muA", "muB", "cA", "cB"}, 1e-2, 3e-2)}
 
 
@@ -196,12 +192,12 @@ def test_d3q19_scalar_lattice_trt_mrt(storage, collision, inplace):
     _close(compare(q, fields(), 12), TOL[storage])
 
 
-def test_d3q19_scalar_lattice_fp16():
+@pytest.mark.parametrize("inplace", [False, True])
+def test_d3q19_scalar_lattice_fp16(inplace):
     p, fields = configs.sedimentation(shape=(24, 24, 40), fraction=0.06, r=(4.0, 6.0), storage="f16")
-    errs = compare(p.with_(lattice="D3Q19"), fields(), 100)
-    scal, tol_s, tol_u = BARS16["f16"]
-    _close({k: v for k, v in errs.items() if k in scal}, tol_s)
-    _close({k: v for k, v in errs.items() if k not in scal}, tol_u)
+    errs = compare(p.with_(lattice="D3Q19", inplace=inplace), fields(), 100)
+    print(f"D3Q19 f16 errors after 100 steps: {errs}")
+    _close(errs, TOL["f16"])
 
 
 @pytest.mark.parametrize("storage", ["f16", "bf16"])

@@ -59,12 +59,43 @@ def test_static_reduce_matches_reduce(case):
         _close(got, ref)
 
 
-def test_static_reduce_rejects_large_flow_lattice():
+@pytest.mark.parametrize("case", ["flow_128", "ripening_384", "couple_f64_1024"])
+def test_static_reduce_rejects_lattices_beyond_the_array(case):
+    # the phi field of a flow lattice (FP32), the bit field of a 3D lattice without flow
+    # (384^3 > 2^25 nodes) and the FP64 phi field of a 2D lattice over half a million nodes
     L, lib = _lib()
-    p, _ = configs.sedimentation(n=128)
+    if case == "flow_128":
+        p, _ = configs.sedimentation(n=128)
+    elif case == "ripening_384":
+        p, _ = configs.ripening(n=384)
+    else:
+        p, _ = configs.diffusion_couple(nx=1024, ny=1024, storage="f64")
     cp = L.make_params(p)
     state = torch.empty(256, dtype=torch.uint8, device="cuda")
     out = (ctypes.c_double * L.NRED)()
     st = lib.lbm_reduce_static(ctypes.byref(cp), ctypes.c_void_p(state.data_ptr()), 0, out, None)
     assert st == L.LBM_ERR_ARG
     assert b"static array" in lib.lbm_last_error(None)
+
+
+def test_static_reduce_just_under_the_array_size():
+    # a 2D D2Q9 lattice of 1,024,000 nodes: FP32 phi field, partials and results fill the
+    # 4 MiB array to within 768 bytes
+    from paper_2409_03401_gb300 import Simulation
+    L, lib = _lib()
+    p, fields = configs.ripening_2d(shape=(1, 1024, 1000))
+    assert lib.lbm_work_bytes(ctypes.byref(L.make_params(p))) == 4 * 1024 * 1024 - 768
+    sim = Simulation(p, *fields())
+    for steps in (2, 0):
+        sim.step(steps)
+        _close(_static_sums(L, lib, sim), sim.sums())
+
+
+def test_static_reduce_rejects_host_memory():
+    L, lib = _lib()
+    p, _ = configs.ripening(shape=(8, 8, 8))
+    cp = L.make_params(p)
+    host = (ctypes.c_double * 4096)()
+    out = (ctypes.c_double * L.NRED)()
+    st = lib.lbm_reduce_static(ctypes.byref(cp), ctypes.cast(host, ctypes.c_void_p), 0, out, None)
+    assert st == L.LBM_ERR_ARG

@@ -40,7 +40,7 @@ class LBMParams:
     nu: float = 0.1
     sigma: float = 1.0e-3
     g: Tuple[float, float, float] = (0.0, 0.0, -1.0e-5)
-    f_scale: float = 1024.0        # 16-bit storage: scale applied to f_k / w_k before rounding
+    f_scale: float = 1024.0        # reserved field of lbm_params (the 16-bit formats have fixed scales)
     collision: str = "BGK"         # flow collision: "BGK" (one rate), "TRT" (two) or "MRT"
     trt_magic: float = 3.0 / 16.0  # TRT: Lambda = (1/omega+ - 1/2)(1/omega- - 1/2)
     # MRT rates of the energy, energy-square, energy-flux, pi and m moments (d'Humieres 2002)
