@@ -23,7 +23,7 @@ int scalar_q(int lattice) {
 }
 bool two_d(int lattice) { return lattice == LBM_D2Q5 || lattice == LBM_D2Q9; }
 // the fused z-marching flow kernel is written for D3Q7 scalar sets
-bool fused_flow(const lbm_params* p) { return p->lattice == LBM_D3Q7; }
+bool fused_flow(const lbm_params* p) { return p->flow && p->lattice == LBM_D3Q7; }
 size_t storage_size(int s) { return s == LBM_F64 ? 8 : (s == LBM_F32 ? 4 : 2); }
 bool is16(int s) { return s == LBM_F16 || s == LBM_BF16; }
 

@@ -63,7 +63,7 @@ class Slab:
     ``ghost_range(...)`` (lbm_slab_planes of them)."""
 
     def __init__(self, params, z0, nzl, phi0, cA0, cB0, device=None, stream=None):
-        device = torch.device(device or ("cuda", torch.cuda.current_device()))
+        device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.lib = _lib.load()
         self.params, self.z0, self.nzl, self.device = params, z0, nzl, device
         self.stream = stream or torch.cuda.current_stream(device)
