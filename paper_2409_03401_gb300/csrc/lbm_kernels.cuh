@@ -39,10 +39,12 @@ struct Nbr {
             c[1][d + 1] = wrap(y + d, P.ny, 0);
         }
     }
+    __device__ __forceinline__ static int wrap2(int q, int n, int wall_lo, int wall_hi) {
+        return q < 0 ? (wall_lo ? -1 : q + n) : (q >= n ? (wall_hi ? -1 : q - n) : q);
+    }
     __device__ __forceinline__ void set_z(int z, const DevParams& P) {
-        c[2][0] = z - 1 < 0 ? (P.wall_zlo ? -1 : z - 1 + P.nz) : z - 1;
-        c[2][1] = z;
-        c[2][2] = z + 1 >= P.nz ? (P.wall_zhi ? -1 : z + 1 - P.nz) : z + 1;
+#pragma unroll
+        for (int d = -1; d <= 1; ++d) c[2][d + 1] = wrap2(z + d, P.nz, P.wall_zlo, P.wall_zhi);
 #pragma unroll
         for (int iz = 0; iz < 3; ++iz)
 #pragma unroll
@@ -143,8 +145,10 @@ struct Node {
             hB[k] = load_scalar<T, SET_H, LAT, Planes<LAT>::HB, 2>(st, k, s, P);
         }
     }
-    template <class A>
-    __device__ __forceinline__ void gather_flow(const StateView& st, const A& ad, const DevParams& P) {
+    // With 16-bit storage ``ref(k, ex, ey, ez, slot)`` gives the FP32 f_0 of the node that
+    // stored the population gathered as k (for k = 0 the node's own f_0).
+    template <class A, class Ref>
+    __device__ __forceinline__ void gather_flow(const StateView& st, const A& ad, const DevParams& P, Ref ref) {
         if constexpr (FLOW) {
 #pragma unroll
             for (int k = 0; k < 19; ++k) {
@@ -152,15 +156,19 @@ struct Node {
                 const Slot s = ad.src(k, ex, ey, ez);
                 if constexpr (is16<T>()) {
                     // f_k / w_k = stored deviation + the writer's f_0 / w_0 (Codec16Pop)
-                    const float* f0 = st.rest + A::kF0In * P.plane;
-                    if (k == 0) f[0] = f0[s.node];
-                    else f[k] = Codec<T>::template load<SET_F>(element<T, 0>(st, k, s), D3Q19::w(k), P) +
-                                f0[ad.writer(k, ex, ey, ez)] * R(1.0 / D3Q19::w(0));
+                    if (k == 0) f[0] = ref(0, 0, 0, 0, s);
+                    else f[k] = fmaf(ref(k, ex, ey, ez, s), float(1.0 / D3Q19::w(0)),
+                                     Codec<T>::template load<SET_F>(element<T, 0>(st, k, s), D3Q19::w(k), P));
                 } else {
                     f[k] = Codec<T>::template load<SET_F>(element<T, 0>(st, k, s), D3Q19::w(k), P);
                 }
             }
         }
+    }
+    template <class A>
+    __device__ __forceinline__ void gather_flow(const StateView& st, const A& ad, const DevParams& P) {
+        const float* f0 = is16<T>() ? st.rest + A::kF0In * P.plane : nullptr;
+        gather_flow(st, ad, P, [&](int k, int ex, int ey, int ez, Slot) { return f0[ad.writer(k, ex, ey, ez)]; });
     }
     template <class A>
     __device__ __forceinline__ void gather(const StateView& st, const A& ad, const DevParams& P) {
@@ -603,17 +611,22 @@ constexpr int kHalo = 2 * (FX + 2) + 2 * FY;    // ring positions outside the ti
 template <class T> constexpr bool park_dc() { return is16<T>(); }
 template <class T> constexpr int spops_n() { return 3 * 7 + (park_dc<T>() ? 3 : 1); }
 
+// With 16-bit storage a second ring holds the FP32 f_0 of the same positions: the reference
+// of the populations each node stored (Codec16Pop), read by the 18 nodes that pull them.
 template <class T>
 __host__ __device__ constexpr size_t fused_smem_bytes() {
     using R = typename RealOf<T>::type;
-    return sizeof(R) * (4 * (FY + 2) * (FX + 2) + 2 * spops_n<T>() * FT);
+    return sizeof(R) * (4 * (FY + 2) * (FX + 2) + 2 * spops_n<T>() * FT) +
+           (is16<T>() ? sizeof(float) * 4 * (FY + 2) * (FX + 2) : 0);
 }
 
 // COLL: the flow collision of this instance. FP32/FP64 storage keeps BGK and TRT in one
 // instance behind a block-uniform branch on P.coll (measured 1 % faster for BGK than a
 // BGK-only instance at this register budget); 16-bit storage and MRT get instances of their
 // own (the 16-bit BGK instance is 6 % faster without the TRT code).
-template <class T, int COLL>
+// SLAB: the lattice is a slab of a z decomposition (planes [z_lo, z_hi), ghost planes
+// beyond); the undivided lattice takes an instance without that code.
+template <class T, int COLL, bool SLAB>
 __global__ void __launch_bounds__(FT, sizeof(typename RealOf<T>::type) == 8 ? 1 : 3)
 fused_flow_kernel(const DevParams P, const StateView src, const StateView dst, int zchunk) {
     constexpr int kColl = (!is16<T>() && COLL != 2) ? -1 : COLL;
@@ -624,12 +637,13 @@ fused_flow_kernel(const DevParams P, const StateView src, const StateView dst, i
     R (*ring)[FY + 2][FX + 2] = reinterpret_cast<R (*)[FY + 2][FX + 2]>(smem_raw);
     R* spops = reinterpret_cast<R*>(smem_raw) + 4 * (FY + 2) * (FX + 2);   // [2][spops_n][FT]
     constexpr int kSPops = spops_n<T>();
+    float (*fring)[FY + 2][FX + 2] = reinterpret_cast<float (*)[FY + 2][FX + 2]>(spops + 2 * kSPops * FT);
     constexpr bool kParkDc = park_dc<T>();
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * FX + tx;
     const int x0 = blockIdx.x * FX, y0 = blockIdx.y * FY;
-    const int zs = P.z_lo + blockIdx.z * zchunk;
-    const int ze = min(zs + zchunk, P.z_hi);
+    const int zs = SLAB ? P.z_lo + blockIdx.z * zchunk : blockIdx.z * zchunk;
+    const int ze = min(zs + zchunk, SLAB ? P.z_hi : P.nz);
     const int x = x0 + tx, y = y0 + ty;
     const bool active = x < P.nx && y < P.ny;
 
@@ -644,8 +658,8 @@ fused_flow_kernel(const DevParams P, const StateView src, const StateView dst, i
         return gx >= 0 && gx < P.nx && gy >= 0 && gy < P.ny;
     };
     auto zwrap = [&](int zz) {
-        if (zz < 0) return P.wall_zlo ? 0 : zz + P.nz;
-        if (zz >= P.nz) return P.wall_zhi ? P.nz - 1 : zz - P.nz;
+        if (zz < 0) return (SLAB ? P.wall_zlo : P.wall_z) ? 0 : zz + P.nz;
+        if (zz >= P.nz) return (SLAB ? P.wall_zhi : P.wall_z) ? P.nz - 1 : zz - P.nz;
         return zz;
     };
     // this thread's own ring column and its halo column (threads tid < kHalo), fixed in z
@@ -672,13 +686,6 @@ fused_flow_kernel(const DevParams P, const StateView src, const StateView dst, i
     // phi (and, for a tile node, its scalar populations in buffer buf) of plane zz
     auto fill = [&](auto fast, int zz, int s, int buf) {
         constexpr bool kFast = decltype(fast)::value;
-        // a slab's neighbouring planes: their phi arrives from the neighbour (phi_ghost)
-        const R* gh = static_cast<const R*>(zz < P.z_lo ? P.phi_ghost[0] : (zz >= P.z_hi ? P.phi_ghost[1] : nullptr));
-        if (gh) {
-            ring[s][ty + 1][tx + 1] = own_ok ? gh[oy * P.nx + ox] : R(0);
-            if (tid < kHalo) ring[s][hyp + 1][hxp + 1] = halo_ok ? gh[hgy * P.nx + hgx] : R(0);
-            return;
-        }
         const int zr = zwrap(zz);
         R v = R(0);
         if (own_ok) {
@@ -708,6 +715,8 @@ fused_flow_kernel(const DevParams P, const StateView src, const StateView dst, i
             }
         }
         ring[s][ty + 1][tx + 1] = v;
+        if constexpr (is16<T>())
+            fring[s][ty + 1][tx + 1] = own_ok ? src.rest[3 * P.plane + node_of(ox, oy, zr, P)] : 0.f;
         if (tid < kHalo) {
             R hv = R(0);
             if (halo_ok) {
@@ -723,12 +732,29 @@ fused_flow_kernel(const DevParams P, const StateView src, const StateView dst, i
                 hv = nd.phi();
             }
             ring[s][hyp + 1][hxp + 1] = hv;
+            if constexpr (is16<T>())
+                fring[s][hyp + 1][hxp + 1] = halo_ok ? src.rest[3 * P.plane + node_of(hgx, hgy, zr, P)] : 0.f;
         }
     };
 
     using Fast = std::true_type;
     using Slow = std::false_type;
+    // a slab's neighbouring planes (z_lo - 1, z_hi): their phi arrives from the neighbour
+    // (phi_ghost), with 16-bit storage their f_0 with the populations
+    auto fill_ghost = [&](const R* gh, int zz, int s) {
+        ring[s][ty + 1][tx + 1] = own_ok ? gh[oy * P.nx + ox] : R(0);
+        if (tid < kHalo) ring[s][hyp + 1][hxp + 1] = halo_ok ? gh[hgy * P.nx + hgx] : R(0);
+        if constexpr (is16<T>()) {
+            const float* f0 = src.rest + 3 * P.plane;
+            fring[s][ty + 1][tx + 1] = own_ok ? f0[node_of(ox, oy, zz, P)] : 0.f;
+            if (tid < kHalo) fring[s][hyp + 1][hxp + 1] = halo_ok ? f0[node_of(hgx, hgy, zz, P)] : 0.f;
+        }
+    };
     auto fill_any = [&](int zz, int s, int buf) {
+        if constexpr (SLAB) {
+            if (zz < P.z_lo && P.phi_ghost[0]) { fill_ghost(static_cast<const R*>(P.phi_ghost[0]), zz, s); return; }
+            if (zz >= P.z_hi && P.phi_ghost[1]) { fill_ghost(static_cast<const R*>(P.phi_ghost[1]), zz, s); return; }
+        }
         if (inner_plane(zwrap(zz))) fill(Fast{}, zz, s, buf);
         else fill(Slow{}, zz, s, buf);
     };
@@ -736,7 +762,11 @@ fused_flow_kernel(const DevParams P, const StateView src, const StateView dst, i
     auto centre = [&](const auto& ad, int z) {
         const int sp = (z - 1) & 3, sc = z & 3, sn = (z + 1) & 3;
         Node<T, LAT_D3Q7, true> nd;
-        nd.gather_flow(src, ad, P);
+        // 16-bit storage: the writers' f_0 from the ring (the node itself across a wall)
+        nd.gather_flow(src, ad, P, [&](int k, int ex, int ey, int ez, Slot s) {
+            if (k == 0 || s.node == ad.self) return fring[sc][ty + 1][tx + 1];
+            return fring[ez > 0 ? sp : (ez < 0 ? sn : sc)][ty + 1 - ey][tx + 1 - ex];
+        });
         const R* spc = spops + (z & 1) * kSPops * FT + tid;
         nd.S = spc[(3 * Q) * FT];
         if constexpr (kParkDc) {
@@ -1120,10 +1150,15 @@ struct Launchers {
         int dev = 0;
         cudaGetDevice(&dev);
         if (dev < 64 && !(configured & (1ull << dev))) {
-            cudaFuncSetAttribute(fused_flow_kernel<T, COLL>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+            cudaFuncSetAttribute(fused_flow_kernel<T, COLL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(smem));
+            cudaFuncSetAttribute(fused_flow_kernel<T, COLL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(smem));
             configured |= 1ull << dev;
         }
-        fused_flow_kernel<T, COLL><<<grid, block, smem, s>>>(P, src, dst, zchunk);
+        const bool slab = P.z_lo != 0 || P.z_hi != P.nz || P.wall_zlo != P.wall_z || P.wall_zhi != P.wall_z;
+        if (slab) fused_flow_kernel<T, COLL, true><<<grid, block, smem, s>>>(P, src, dst, zchunk);
+        else fused_flow_kernel<T, COLL, false><<<grid, block, smem, s>>>(P, src, dst, zchunk);
     }
     template <int LAT, bool FLOW>
     static void fields(const DevParams& P, const StateView& st, int mode, void* phi_work, FieldPtrs out,
