@@ -52,11 +52,8 @@ typedef enum { LBM_D2Q5 = 0, LBM_D3Q7 = 1, LBM_D3Q19 = 2, LBM_D2Q9 = 3 } lbm_lat
  * population of the node that stored it, x_k = f_k / w_k - f_0 / w_0 (f_0 ~ w_0 p_h, so the
  * pressure is not rounded). The rest populations g_0, h^A_0, h^B_0, f_0 stay FP32 (in place,
  * f_0 alternates between two planes by the parity of the time level).
- *   LBM_F16: g in 16-bit fixed point over [-1, 1) (step 2^-15); f (as 8 x) and h in a 16-bit
- *            float with 1 sign, 4 exponent and 11 mantissa bits, exponent bias 15, subnormals,
- *            no infinities (the "FP16C" layout of Lehmann et al., Phys. Rev. E 106, 015308,
- *            2022). Both saturate: |u| must stay below about 0.15 and |h_k / w_k| below 2,
- *            far outside the regime of a stable run.
+ *   LBM_F16: g in 16-bit fixed point over [-1, 1) (step 2^-15, saturating: a stable run
+ *            stays far inside); f as IEEE FP16 of 1024 x_k, h as IEEE FP16 of 64 x_k.
  *   LBM_BF16: every x_k as BF16 (8-bit significand).
  * Every step sets the rest populations of g and h to their set's conserved total at the node
  * (phi~ + S, c - c_0^eq) minus the moving populations as stored, so phi, c^A and c^B are

@@ -817,7 +817,7 @@ const char* lbm_last_error(const lbm_ctx* c) {
 
 const char* lbm_build_info(void) {
     return "gplbm sm_103a: fused collide-stream (AA in place; two-buffer z-marching with flow); "
-           "storage f64/f32/f16 (fixed point g, 1-4-11 floats f and h)/bf16; scalar lattices "
+           "storage f64/f32/f16 (fixed-point g; FP16 f, h; f against its writer's f_0)/bf16; scalar lattices "
            "D2Q5/D2Q9/D3Q7/D3Q19, flow D3Q19 BGK/TRT/MRT; adjoint";
 }
 

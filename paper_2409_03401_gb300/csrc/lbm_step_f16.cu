@@ -1,5 +1,5 @@
 // Coupled-step kernels instantiated for the 16-bit Store16 population storage (fixed point
-// for g, 1-4-11 floats for f and h; see Codec16 in lbm_device.cuh).
+// for g, IEEE FP16 for f and h; see Codec16 in lbm_device.cuh).
 #include "lbm_kernels.cuh"
 
 namespace lbm {

@@ -118,10 +118,10 @@ def with_theta(p, theta):
     return p.with_(M=((d0, d0), (d1, d1)), M_phi=mphi)
 
 
-def adjoint_problem(n=128, storage="f32", shape=None, seed=5, theta=THETA_EVAL):
+def adjoint_problem(n=128, storage="f32", shape=None, seed=5, theta=THETA_EVAL, supersaturation=SUPERSATURATION):
     nz, ny, nx = shape or (n, n, n)
     p = with_theta(LBMParams(nx=nx, ny=ny, nz=nz, lattice="D3Q7", flow=False, storage=storage), theta)
-    return p, _droplet_workload(p, 0.15, 4.0, 10.0, seed)
+    return p, _droplet_workload(p, 0.15, 4.0, 10.0, seed, supersaturation=supersaturation)
 
 
 CONFIGS = {
