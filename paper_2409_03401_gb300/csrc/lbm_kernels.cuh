@@ -311,27 +311,68 @@ __device__ __forceinline__ R edot(int ex, int ey, int ez, R vx, R vy, R vz) {
 // choose between BGK and TRT only, -2 reads it to choose among all three.
 // MRT on the D3Q19 moment basis: d = f - f^eq, dm_i = (rate_i / |M_i|^2) sum_k M_ik d_k,
 // f*_k = f_k - sum_i M_ik dm_i + F_k (M^-1 = M^T diag(1 / |M_i|^2)).
+// The basis rows are even or odd under k -> opp(k), so the transform runs on the pair sums
+// s = d_a + d_opp(a) (even rows) and differences t = d_a - d_opp(a) (odd rows), and the
+// back-transform gives r_a = E + O, r_opp(a) = E - O: about half the products of the dense
+// 19 x 19 forms. put(0, r_0) comes first, then the pairs in order.
+__host__ __device__ constexpr bool mrt_even_row_of_basis(int i) {
+    for (int k = 1; k < 19; ++k)
+        if (MRT19::m(i, k) != MRT19::m(i, opp(k))) return false;
+    return true;
+}
+// even rows as a mask, so that the test folds to a constant in the unrolled loops (a loop
+// evaluated per node would run the basis in FP64 at run time)
+constexpr unsigned kMrtEvenRows = (1u << 0) | (1u << 1) | (1u << 2) | (1u << 9) | (1u << 10) | (1u << 11) |
+                                  (1u << 12) | (1u << 13) | (1u << 14) | (1u << 15);
+__host__ __device__ constexpr bool mrt_mask_matches_basis() {
+    for (int i = 0; i < 19; ++i)
+        if (mrt_even_row_of_basis(i) != bool((kMrtEvenRows >> i) & 1u)) return false;
+    return true;
+}
+static_assert(mrt_mask_matches_basis(), "even/odd rows of the D3Q19 moment basis");
+__host__ __device__ constexpr bool mrt_even_row(int i) { return (kMrtEvenRows >> i) & 1u; }
 template <class R, class Pre, class Post>
 __device__ __forceinline__ void mrt_relax(const DevParams& P, Pre d_of, Post put) {
-    R d[19];
+    R d0 = d_of(0);
+    R s[9], t[9];
 #pragma unroll
-    for (int k = 0; k < 19; ++k) d[k] = d_of(k);
+    for (int p = 0; p < 9; ++p) {
+        const R a = d_of(2 * p + 1), b = d_of(2 * p + 2);
+        s[p] = a + b;
+        t[p] = a - b;
+    }
     R dm[19];
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
-        R a = R(0);
+        R acc = R(0);
+        if (mrt_even_row(i)) {
+            if (MRT19::m(i, 0) != 0.0) acc = R(MRT19::m(i, 0)) * d0;
 #pragma unroll
-        for (int k = 0; k < 19; ++k)
-            if (MRT19::m(i, k) != 0.0) a += R(MRT19::m(i, k)) * d[k];
-        dm[i] = a * coef<R>(P).mrt[i];
+            for (int p = 0; p < 9; ++p)
+                if (MRT19::m(i, 2 * p + 1) != 0.0) acc += R(MRT19::m(i, 2 * p + 1)) * s[p];
+        } else {
+#pragma unroll
+            for (int p = 0; p < 9; ++p)
+                if (MRT19::m(i, 2 * p + 1) != 0.0) acc += R(MRT19::m(i, 2 * p + 1)) * t[p];
+        }
+        dm[i] = acc * coef<R>(P).mrt[i];
     }
+    R r0 = R(0);
 #pragma unroll
-    for (int k = 0; k < 19; ++k) {
-        R r = R(0);
+    for (int i = 0; i < 19; ++i)
+        if (mrt_even_row(i) && MRT19::m(i, 0) != 0.0) r0 += R(MRT19::m(i, 0)) * dm[i];
+    put(0, r0);
 #pragma unroll
-        for (int i = 0; i < 19; ++i)
-            if (MRT19::m(i, k) != 0.0) r += R(MRT19::m(i, k)) * dm[i];
-        put(k, r);
+    for (int p = 0; p < 9; ++p) {
+        R e = R(0), o = R(0);
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            if (MRT19::m(i, 2 * p + 1) == 0.0) continue;
+            if (mrt_even_row(i)) e += R(MRT19::m(i, 2 * p + 1)) * dm[i];
+            else o += R(MRT19::m(i, 2 * p + 1)) * dm[i];
+        }
+        put(2 * p + 1, e + o);
+        put(2 * p + 2, e - o);
     }
 }
 
@@ -345,184 +386,202 @@ __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, type
     using L = Scalar<LAT>;
     constexpr int Q = L::Q;
     const int self = ad.self;
-    if constexpr (FLOW) {
-        const R ph = nd.flow_p();
-        const R usq = ux * ux + uy * uy + uz * uz;
-        const R Ac = R(1) - R(1.5) * usq;
-        const R Bc = ph - R(0.5) * usq;
-        const R uF = ux * Fx + uy * Fy + uz * Fz;
-        const R omf = coef<R>(P).om_f;
-        // G = F_k / w_k (Eqs. 37-38) and E = f^eq_k / w_k (Eq. 39) of direction k
-        auto force_eq = [&](int k, R& G, R& E) {
-            const int ex = D3Q19::ex(k), ey = D3Q19::ey(k), ez = D3Q19::ez(k);
-            const R cu = edot(ex, ey, ez, ux, uy, uz);
-            G = (Ac + cu * (R(3) + R(4.5) * cu)) * (edot(ex, ey, ez, Fx, Fy, Fz) - uF);
-            E = Bc + cu * (R(1) + R(1.5) * cu) - R(0.5) * G;
-        };
-        if constexpr (!is16<T>()) {
-            auto put = [&](int k, R post) {
-                const Slot s = ad.dst(k, D3Q19::ex(k), D3Q19::ey(k), D3Q19::ez(k));
-                *element<T, 0>(out, k, s) = post;
-            };
-            // F_k and f^eq_k in natural units
-            auto force_eq_w = [&](int k, R& Fk, R& feq) {
+    auto collide_f = [&]() {
+        if constexpr (FLOW) {
+            const R ph = nd.flow_p();
+            const R usq = ux * ux + uy * uy + uz * uz;
+            const R Ac = R(1) - R(1.5) * usq;
+            const R Bc = ph - R(0.5) * usq;
+            const R uF = ux * Fx + uy * Fy + uz * Fz;
+            const R omf = coef<R>(P).om_f;
+            // G = F_k / w_k (Eqs. 37-38) and E = f^eq_k / w_k (Eq. 39) of direction k
+            auto force_eq = [&](int k, R& G, R& E) {
                 const int ex = D3Q19::ex(k), ey = D3Q19::ey(k), ez = D3Q19::ez(k);
-                const R w = R(D3Q19::w(k));
                 const R cu = edot(ex, ey, ez, ux, uy, uz);
-                Fk = w * (Ac + cu * (R(3) + R(4.5) * cu)) * (edot(ex, ey, ez, Fx, Fy, Fz) - uF);
-                feq = w * (Bc + cu * (R(1) + R(1.5) * cu)) - R(0.5) * Fk;
+                G = (Ac + cu * (R(3) + R(4.5) * cu)) * (edot(ex, ey, ez, Fx, Fy, Fz) - uF);
+                E = Bc + cu * (R(1) + R(1.5) * cu) - R(0.5) * G;
             };
-            const int coll = COLL >= 0 ? COLL : (COLL == -1 && P.coll == 2 ? 0 : P.coll);
-            if (coll == 0) {                                  // BGK, Eq. 36
-#pragma unroll
-                for (int k = 0; k < 19; ++k) {
-                    R Fk, feq;
-                    force_eq_w(k, Fk, feq);
-                    put(k, nd.f[k] - omf * (nd.f[k] - feq) + Fk);
-                }
-            } else if ((COLL == 2 || COLL == -2) && coll == 2) {   // multiple relaxation times
-                R Fs[19];
-                mrt_relax<R>(P, [&](int k) {
-                    R feq;
-                    force_eq_w(k, Fs[k], feq);
-                    return nd.f[k] - feq;
-                }, [&](int k, R r) { put(k, nd.f[k] - r + Fs[k]); });
-            } else {                                          // two relaxation times
-                const R omm = coef<R>(P).om_fm;
-                R F0, feq0;
-                force_eq_w(0, F0, feq0);
-                put(0, nd.f[0] - omf * (nd.f[0] - feq0) + F0);
-#pragma unroll
-                for (int k = 1; k < 19; k += 2) {             // pairs (k, opp(k) = k + 1)
-                    R Fa, ea, Fb, eb;
-                    force_eq_w(k, Fa, ea);
-                    force_eq_w(k + 1, Fb, eb);
-                    const R da = nd.f[k] - ea, db = nd.f[k + 1] - eb;
-                    const R even = R(0.5) * (da + db), odd = R(0.5) * (da - db);
-                    put(k, nd.f[k] - omf * even - omm * odd + Fa);
-                    put(k + 1, nd.f[k + 1] - omf * even + omm * odd + Fb);
-                }
-            }
-        } else {
-            // 16-bit storage: nd.f[k] = f_k / w_k for k > 0 (the writer's reference added back
-            // on load), nd.f[0] = f_0. The updates below are those of the FP32 branch divided by
-            // w_k. f*_0 is stored first, in FP32, and is the reference of every moving
-            // population this node stores: x*_k - f*_0 / w_0 is what gets rounded.
-            using C = Codec<T>;
-            R ref = R(0);
-            auto put0 = [&](R f0post) {
-                const float f0s = float(f0post);
-                out.rest[A::kF0Out * P.plane + self] = f0s;
-                ref = R(f0s) * R(1.0 / D3Q19::w(0));
-            };
-            auto put = [&](int k, R x) {
-                const Slot sl = ad.dst(k, D3Q19::ex(k), D3Q19::ey(k), D3Q19::ez(k));
-                *element<T, 0>(out, k, sl) = C::template enc<SET_F>(float(x - ref));
-            };
-            const R w0 = R(D3Q19::w(0));
-            const int coll = COLL >= 0 ? COLL : (COLL == -1 && P.coll == 2 ? 0 : P.coll);
-            if ((COLL == 2 || COLL == -2) && coll == 2) {
-                // MRT mixes directions: run it on the populations in natural units
-                R Fs[19];
-                mrt_relax<R>(P, [&](int k) {
-                    R G, E;
-                    force_eq(k, G, E);
+            if constexpr (!is16<T>()) {
+                auto put = [&](int k, R post) {
+                    const Slot s = ad.dst(k, D3Q19::ex(k), D3Q19::ey(k), D3Q19::ez(k));
+                    *element<T, 0>(out, k, s) = post;
+                };
+                // F_k and f^eq_k in natural units
+                auto force_eq_w = [&](int k, R& Fk, R& feq) {
+                    const int ex = D3Q19::ex(k), ey = D3Q19::ey(k), ez = D3Q19::ez(k);
                     const R w = R(D3Q19::w(k));
-                    Fs[k] = w * G;
-                    return k == 0 ? nd.f[0] - w * E : w * (nd.f[k] - E);
-                }, [&](int k, R r) {
-                    if (k == 0) put0(nd.f[0] - r + Fs[0]);
-                    else put(k, nd.f[k] + (Fs[k] - r) * R(1.0 / D3Q19::w(k)));
-                });
+                    const R cu = edot(ex, ey, ez, ux, uy, uz);
+                    Fk = w * (Ac + cu * (R(3) + R(4.5) * cu)) * (edot(ex, ey, ez, Fx, Fy, Fz) - uF);
+                    feq = w * (Bc + cu * (R(1) + R(1.5) * cu)) - R(0.5) * Fk;
+                };
+                const int coll = COLL >= 0 ? COLL : (COLL == -1 && P.coll == 2 ? 0 : P.coll);
+                if (coll == 0) {                                  // BGK, Eq. 36
+    #pragma unroll
+                    for (int k = 0; k < 19; ++k) {
+                        R Fk, feq;
+                        force_eq_w(k, Fk, feq);
+                        put(k, nd.f[k] - omf * (nd.f[k] - feq) + Fk);
+                    }
+                } else if ((COLL == 2 || COLL == -2) && coll == 2) {   // multiple relaxation times
+                    R fF[19];                                  // f_k + F_k: f_k is dead after d_k
+                    mrt_relax<R>(P, [&](int k) {
+                        R Fk, feq;
+                        force_eq_w(k, Fk, feq);
+                        fF[k] = nd.f[k] + Fk;
+                        return nd.f[k] - feq;
+                    }, [&](int k, R r) { put(k, fF[k] - r); });
+                } else {                                          // two relaxation times
+                    const R omm = coef<R>(P).om_fm;
+                    R F0, feq0;
+                    force_eq_w(0, F0, feq0);
+                    put(0, nd.f[0] - omf * (nd.f[0] - feq0) + F0);
+    #pragma unroll
+                    for (int k = 1; k < 19; k += 2) {             // pairs (k, opp(k) = k + 1)
+                        R Fa, ea, Fb, eb;
+                        force_eq_w(k, Fa, ea);
+                        force_eq_w(k + 1, Fb, eb);
+                        const R da = nd.f[k] - ea, db = nd.f[k + 1] - eb;
+                        const R even = R(0.5) * (da + db), odd = R(0.5) * (da - db);
+                        put(k, nd.f[k] - omf * even - omm * odd + Fa);
+                        put(k + 1, nd.f[k + 1] - omf * even + omm * odd + Fb);
+                    }
+                }
             } else {
-                R G0, E0;
-                force_eq(0, G0, E0);
-                put0(nd.f[0] - omf * (nd.f[0] - w0 * E0) + w0 * G0);
-                if (coll == 0) {
-#pragma unroll
-                    for (int k = 1; k < 19; ++k) {
+                // 16-bit storage: nd.f[k] = f_k / w_k for k > 0 (the writer's reference added back
+                // on load), nd.f[0] = f_0. The updates below are those of the FP32 branch divided by
+                // w_k. f*_0 is stored first, in FP32, and is the reference of every moving
+                // population this node stores: x*_k - f*_0 / w_0 is what gets rounded.
+                using C = Codec<T>;
+                R ref = R(0);
+                auto put0 = [&](R f0post) {
+                    const float f0s = float(f0post);
+                    out.rest[A::kF0Out * P.plane + self] = f0s;
+                    ref = R(f0s) * R(1.0 / D3Q19::w(0));
+                };
+                auto put = [&](int k, R x) {
+                    const Slot sl = ad.dst(k, D3Q19::ex(k), D3Q19::ey(k), D3Q19::ez(k));
+                    *element<T, 0>(out, k, sl) = C::template enc<SET_F>(float(x - ref));
+                };
+                const R w0 = R(D3Q19::w(0));
+                const int coll = COLL >= 0 ? COLL : (COLL == -1 && P.coll == 2 ? 0 : P.coll);
+                if ((COLL == 2 || COLL == -2) && coll == 2) {
+                    // MRT mixes directions: run it on the populations in natural units
+                    R fF[19];                                  // per unit weight, f_k / w_k + G_k
+                    mrt_relax<R>(P, [&](int k) {
                         R G, E;
                         force_eq(k, G, E);
-                        put(k, nd.f[k] - omf * (nd.f[k] - E) + G);
-                    }
+                        const R w = R(D3Q19::w(k));
+                        if (k == 0) {
+                            fF[0] = nd.f[0] + w * G;
+                            return nd.f[0] - w * E;
+                        }
+                        fF[k] = nd.f[k] + G;
+                        return w * (nd.f[k] - E);
+                    }, [&](int k, R r) {
+                        if (k == 0) put0(fF[0] - r);
+                        else put(k, fF[k] - r * R(1.0 / D3Q19::w(k)));
+                    });
                 } else {
-                    const R omm = coef<R>(P).om_fm;
-#pragma unroll
-                    for (int k = 1; k < 19; k += 2) {
-                        R Ga, Ea, Gb, Eb;
-                        force_eq(k, Ga, Ea);
-                        force_eq(k + 1, Gb, Eb);
-                        const R da = nd.f[k] - Ea, db = nd.f[k + 1] - Eb;
-                        const R even = R(0.5) * (da + db), odd = R(0.5) * (da - db);
-                        put(k, nd.f[k] - omf * even - omm * odd + Ga);
-                        put(k + 1, nd.f[k + 1] - omf * even + omm * odd + Gb);
+                    R G0, E0;
+                    force_eq(0, G0, E0);
+                    put0(nd.f[0] - omf * (nd.f[0] - w0 * E0) + w0 * G0);
+                    if (coll == 0) {
+    #pragma unroll
+                        for (int k = 1; k < 19; ++k) {
+                            R G, E;
+                            force_eq(k, G, E);
+                            put(k, nd.f[k] - omf * (nd.f[k] - E) + G);
+                        }
+                    } else {
+                        const R omm = coef<R>(P).om_fm;
+    #pragma unroll
+                        for (int k = 1; k < 19; k += 2) {
+                            R Ga, Ea, Gb, Eb;
+                            force_eq(k, Ga, Ea);
+                            force_eq(k + 1, Gb, Eb);
+                            const R da = nd.f[k] - Ea, db = nd.f[k + 1] - Eb;
+                            const R even = R(0.5) * (da + db), odd = R(0.5) * (da - db);
+                            put(k, nd.f[k] - omf * even - omm * odd + Ga);
+                            put(k + 1, nd.f[k + 1] - omf * even + omm * odd + Gb);
+                        }
                     }
                 }
             }
         }
-    }
-    const R p = interp_p(phi);
-    const R muA = closure_dev(nd.dcA, p, 0, P);
-    const R muB = closure_dev(nd.dcB, p, 1, P);
-    const R inv_cs2 = R(1.0 / L::cs2());
-    const R omg = coef<R>(P).om_g;
-    const R MA = coef<R>(P).M0[0] * (R(1) - phi) + coef<R>(P).M1[0] * phi;     // §2.3
-    const R MB = coef<R>(P).M0[1] * (R(1) - phi) + coef<R>(P).M1[1] * phi;
-    const R omA = recip(MA * inv_cs2 + R(0.5));                      // tau_h = M / c_s^2
-    const R omB = recip(MB * inv_cs2 + R(0.5));
-    const R ga = phi - R(0.5) * nd.S;                                 // g^eq = w (ga + gb cu)
-    const R gb = phi * inv_cs2;
-    const R cAu = nd.cA(P) * inv_cs2, cBu = nd.cB(P) * inv_cs2;
-    // rest populations (natural units in every storage), stored last
-    R g0, hA0, hB0;
-    if constexpr (!is16<T>()) {
-#pragma unroll
-        for (int k = 0; k < Q; ++k) {
-            const int ex = L::ex(k), ey = L::ey(k), ez = L::ez(k);
-            const R w = R(L::w(k));
-            const R cu = edot(ex, ey, ez, ux, uy, uz);
-            const R geq = w * (ga + gb * cu);
-            const R gpost = nd.g[k] - omg * (nd.g[k] - geq) + w * nd.S;
-            if (k == 0) {                                             // h_0 shifted by c_0^eq
-                g0 = gpost;
-                hA0 = nd.hA[0] - omA * (nd.hA[0] - (nd.dcA - (R(1) - w) * muA));
-                hB0 = nd.hB[0] - omB * (nd.hB[0] - (nd.dcB - (R(1) - w) * muB));
-                continue;
+    };
+    auto collide_s = [&]() {
+        const R p = interp_p(phi);
+        const R muA = closure_dev(nd.dcA, p, 0, P);
+        const R muB = closure_dev(nd.dcB, p, 1, P);
+        const R inv_cs2 = R(1.0 / L::cs2());
+        const R omg = coef<R>(P).om_g;
+        const R MA = coef<R>(P).M0[0] * (R(1) - phi) + coef<R>(P).M1[0] * phi;     // §2.3
+        const R MB = coef<R>(P).M0[1] * (R(1) - phi) + coef<R>(P).M1[1] * phi;
+        const R omA = recip(MA * inv_cs2 + R(0.5));                      // tau_h = M / c_s^2
+        const R omB = recip(MB * inv_cs2 + R(0.5));
+        const R ga = phi - R(0.5) * nd.S;                                 // g^eq = w (ga + gb cu)
+        const R gb = phi * inv_cs2;
+        const R cAu = nd.cA(P) * inv_cs2, cBu = nd.cB(P) * inv_cs2;
+        // rest populations (natural units in every storage), stored last
+        R g0, hA0, hB0;
+        if constexpr (!is16<T>()) {
+    #pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                const int ex = L::ex(k), ey = L::ey(k), ez = L::ez(k);
+                const R w = R(L::w(k));
+                const R cu = edot(ex, ey, ez, ux, uy, uz);
+                const R geq = w * (ga + gb * cu);
+                const R gpost = nd.g[k] - omg * (nd.g[k] - geq) + w * nd.S;
+                if (k == 0) {                                             // h_0 shifted by c_0^eq
+                    g0 = gpost;
+                    hA0 = nd.hA[0] - omA * (nd.hA[0] - (nd.dcA - (R(1) - w) * muA));
+                    hB0 = nd.hB[0] - omB * (nd.hB[0] - (nd.dcB - (R(1) - w) * muB));
+                    continue;
+                }
+                const Slot s = ad.dst(k, ex, ey, ez);
+                *element<T, Planes<LAT>::G>(out, k, s) = gpost;
+                *element<T, Planes<LAT>::HA>(out, k, s) = nd.hA[k] - omA * (nd.hA[k] - w * (muA + cAu * cu));
+                *element<T, Planes<LAT>::HB>(out, k, s) = nd.hB[k] - omB * (nd.hB[k] - w * (muB + cBu * cu));
             }
-            const Slot s = ad.dst(k, ex, ey, ez);
-            *element<T, Planes<LAT>::G>(out, k, s) = gpost;
-            *element<T, Planes<LAT>::HA>(out, k, s) = nd.hA[k] - omA * (nd.hA[k] - w * (muA + cAu * cu));
-            *element<T, Planes<LAT>::HB>(out, k, s) = nd.hB[k] - omB * (nd.hB[k] - w * (muB + cBu * cu));
+        } else {
+            // the collisions keep sum g = phi~ + S and sum h = c - c_0^eq (Eqs. 47-48, 51 with the
+            // shifted h_0); each rest population takes that total minus what the moving ones stored
+            g0 = phi + R(0.5) * nd.S - R(0.5 * (1.0 - L::w(0)));       // phi~ + S = phi + S/2
+            hA0 = nd.dcA;
+            hB0 = nd.dcB;
+            // per unit weight: g = w (x + 1/2) gives x* = x - om (x + 1/2 - ga - gb cu) + S, and
+            // h = w x gives x* = x - om (x - (mu + c cu / cs2))
+            using C = Codec<T>;
+            const R gq = R(0.5) - ga;
+            const R mA = muA, mB = muB;
+            const R cA = cAu, cB = cBu;
+    #pragma unroll
+            for (int k = 1; k < Q; ++k) {
+                const int ex = L::ex(k), ey = L::ey(k), ez = L::ez(k);
+                const R cu = edot(ex, ey, ez, ux, uy, uz);
+                const Slot s = ad.dst(k, ex, ey, ez);
+                const R qg = nd.g[k] - omg * (nd.g[k] + gq - gb * cu) + nd.S;
+                const R qA = nd.hA[k] - omA * (nd.hA[k] - (mA + cA * cu));
+                const R qB = nd.hB[k] - omB * (nd.hB[k] - (mB + cB * cu));
+                g0 -= R(L::w(k)) * C::template store_back<SET_G>(element<T, Planes<LAT>::G>(out, k, s), qg);
+                hA0 -= R(L::w(k)) * C::template store_back<SET_H>(element<T, Planes<LAT>::HA>(out, k, s), qA);
+                hB0 -= R(L::w(k)) * C::template store_back<SET_H>(element<T, Planes<LAT>::HB>(out, k, s), qB);
+            }
         }
+        const Slot s0{self, 0};
+        store_scalar<T, SET_G, LAT, Planes<LAT>::G, 0>(out, 0, s0, g0, P);
+        store_scalar<T, SET_H, LAT, Planes<LAT>::HA, 1>(out, 0, s0, hA0, P);
+        store_scalar<T, SET_H, LAT, Planes<LAT>::HB, 2>(out, 0, s0, hB0, P);
+    };
+    // MRT instances collide the scalar sets first: their populations are dead before the
+    // moment transform needs the registers
+    if constexpr (COLL == 2) {
+        collide_s();
+        collide_f();
     } else {
-        // the collisions keep sum g = phi~ + S and sum h = c - c_0^eq (Eqs. 47-48, 51 with the
-        // shifted h_0); each rest population takes that total minus what the moving ones stored
-        g0 = phi + R(0.5) * nd.S - R(0.5 * (1.0 - L::w(0)));       // phi~ + S = phi + S/2
-        hA0 = nd.dcA;
-        hB0 = nd.dcB;
-        // per unit weight: g = w (x + 1/2) gives x* = x - om (x + 1/2 - ga - gb cu) + S, and
-        // h = w x gives x* = x - om (x - (mu + c cu / cs2))
-        using C = Codec<T>;
-        const R gq = R(0.5) - ga;
-        const R mA = muA, mB = muB;
-        const R cA = cAu, cB = cBu;
-#pragma unroll
-        for (int k = 1; k < Q; ++k) {
-            const int ex = L::ex(k), ey = L::ey(k), ez = L::ez(k);
-            const R cu = edot(ex, ey, ez, ux, uy, uz);
-            const Slot s = ad.dst(k, ex, ey, ez);
-            const R qg = nd.g[k] - omg * (nd.g[k] + gq - gb * cu) + nd.S;
-            const R qA = nd.hA[k] - omA * (nd.hA[k] - (mA + cA * cu));
-            const R qB = nd.hB[k] - omB * (nd.hB[k] - (mB + cB * cu));
-            g0 -= R(L::w(k)) * C::template store_back<SET_G>(element<T, Planes<LAT>::G>(out, k, s), qg);
-            hA0 -= R(L::w(k)) * C::template store_back<SET_H>(element<T, Planes<LAT>::HA>(out, k, s), qA);
-            hB0 -= R(L::w(k)) * C::template store_back<SET_H>(element<T, Planes<LAT>::HB>(out, k, s), qB);
-        }
+        collide_f();
+        collide_s();
     }
-    const Slot s0{self, 0};
-    store_scalar<T, SET_G, LAT, Planes<LAT>::G, 0>(out, 0, s0, g0, P);
-    store_scalar<T, SET_H, LAT, Planes<LAT>::HA, 1>(out, 0, s0, hA0, P);
-    store_scalar<T, SET_H, LAT, Planes<LAT>::HB, 2>(out, 0, s0, hB0, P);
 }
 
 // ------------------------------------------------------------------------------------
@@ -626,8 +685,13 @@ __host__ __device__ constexpr size_t fused_smem_bytes() {
 // own (the 16-bit BGK instance is 6 % faster without the TRT code).
 // SLAB: the lattice is a slab of a z decomposition (planes [z_lo, z_hi), ghost planes
 // beyond); the undivided lattice takes an instance without that code.
+// Blocks per SM the register budget is cut for: three (80 registers). (MRT at two blocks and
+// 128 registers, without spills, measured 8 % slower than three blocks with a few spills.)
+template <class T, int COLL>
+constexpr int fused_min_blocks() { return sizeof(typename RealOf<T>::type) == 8 ? 1 : 3; }
+
 template <class T, int COLL, bool SLAB>
-__global__ void __launch_bounds__(FT, sizeof(typename RealOf<T>::type) == 8 ? 1 : 3)
+__global__ void __launch_bounds__(FT, fused_min_blocks<T, COLL>())
 fused_flow_kernel(const DevParams P, const StateView src, const StateView dst, int zchunk) {
     constexpr int kColl = (!is16<T>() && COLL != 2) ? -1 : COLL;
     using R = typename RealOf<T>::type;
@@ -809,11 +873,14 @@ fused_flow_kernel(const DevParams P, const StateView src, const StateView dst, i
 }
 
 // ------------------------------------------------------------------------------------
-// Initial populations at rest, computed in FP64 then stored (Eqs. 47, 51 and 37-39 at
-// u = 0, p_h = 0). Each node evaluates its phi_0-derived quantities once and stores its
-// population k in the slot its own first gather of k will read (Addr<MODE>::src): its own
-// slot k for AA_EVEN; for PULL slot k of node x - e_k, or, when that lies beyond a wall,
-// its own slot opp(k). Every slot has exactly one writer.
+// Initial populations at rest (Eqs. 47, 51 and 37-39 at u = 0, p_h = 0), in the storage's
+// arithmetic type (FP32 for FP32 and 16-bit storage, like every later step; GB300's FP64 pipe
+// would make this kernel several steps long). The FP64 inputs are read once and the
+// compositions shifted by c_0^eq in FP64 before the conversion, so the closure's cancellation
+// starts from the exact deviations. Each node evaluates its phi_0-derived quantities once and
+// stores its population k in the slot its own first gather of k will read (Addr<MODE>::src):
+// its own slot k for AA_EVEN; for PULL slot k of node x - e_k, or, when that lies beyond a
+// wall, its own slot opp(k). Every slot has exactly one writer.
 template <class T, int LAT, bool FLOW, int MODE>
 __global__ void __launch_bounds__(kBlockX)
 init_kernel(const DevParams P, const StateView st, const double* __restrict__ phi0,
@@ -826,30 +893,31 @@ init_kernel(const DevParams P, const StateView st, const double* __restrict__ ph
     Addr<MODE> ad;
     ad.self = node_of(x, y, z, P);
     ad.nb.init(x, y, z, P);
-    const double ph = phi0[ad.self];
-    const double pp = interp_p(ph);
-    const double dA = cA0[ad.self] - P.c0[0], dB = cB0[ad.self] - P.c0[1];
-    const double muA = closure_dev(dA, pp, 0, P), muB = closure_dev(dB, pp, 1, P);
-    const double S = source(ph, muA, muB, P);
+    const R ph = R(phi0[ad.self]);
+    const R pp = interp_p(ph);
+    const R dA = R(cA0[ad.self] - P.c0[0]), dB = R(cB0[ad.self] - P.c0[1]);
+    const R muA = closure_dev(dA, pp, 0, P), muB = closure_dev(dB, pp, 1, P);
+    const R S = source(ph, muA, muB, P);
 #pragma unroll
     for (int k = 0; k < L::Q; ++k) {
-        const double w = L::w(k);
+        const R w = R(L::w(k));
         const Slot s = ad.src(k, L::ex(k), L::ey(k), L::ez(k));
-        store_scalar<T, SET_G, LAT, Planes<LAT>::G, 0>(st, k, s, R(w * ph - 0.5 * w * S), P);   // Eq. 47
-        const double hA = k == 0 ? dA - (1.0 - w) * muA : w * muA;                         // Eq. 51,
-        const double hB = k == 0 ? dB - (1.0 - w) * muB : w * muB;                         // h_0 shifted
-        store_scalar<T, SET_H, LAT, Planes<LAT>::HA, 1>(st, k, s, R(hA), P);
-        store_scalar<T, SET_H, LAT, Planes<LAT>::HB, 2>(st, k, s, R(hB), P);
+        store_scalar<T, SET_G, LAT, Planes<LAT>::G, 0>(st, k, s, w * ph - R(0.5) * w * S, P);   // Eq. 47
+        const R hA = k == 0 ? dA - (R(1) - w) * muA : w * muA;                               // Eq. 51,
+        const R hB = k == 0 ? dB - (R(1) - w) * muB : w * muB;                               // h_0 shifted
+        store_scalar<T, SET_H, LAT, Planes<LAT>::HA, 1>(st, k, s, hA, P);
+        store_scalar<T, SET_H, LAT, Planes<LAT>::HB, 2>(st, k, s, hB, P);
     }
     if constexpr (FLOW) {
-        double gx, gy, gz, lap;
-        stencil([&](int dx, int dy, int dz) { return ad.phi(phi0, dx, dy, dz); }, ph, gx, gy, gz, lap);
-        const double br = P.sw15 * (dwell_d(ph) * P.inv_W2 - lap);
-        const double Fx = br * gx + ph * P.g[0], Fy = br * gy + ph * P.g[1], Fz = br * gz + ph * P.g[2];
+        R gx, gy, gz, lap;
+        stencil([&](int dx, int dy, int dz) { return R(ad.phi(phi0, dx, dy, dz)); }, ph, gx, gy, gz, lap);
+        const R br = coef<R>(P).sw15 * (dwell_d(ph) * coef<R>(P).inv_W2 - lap);
+        const R Fx = br * gx + ph * coef<R>(P).g[0], Fy = br * gy + ph * coef<R>(P).g[1];
+        const R Fz = br * gz + ph * coef<R>(P).g[2];
 #pragma unroll
         for (int k = 0; k < 19; ++k) {
             const int ex = D3Q19::ex(k), ey = D3Q19::ey(k), ez = D3Q19::ez(k);
-            const R v = R(-0.5 * D3Q19::w(k) * (ex * Fx + ey * Fy + ez * Fz));          // Eqs. 37-39
+            const R v = R(-0.5 * D3Q19::w(k)) * edot(ex, ey, ez, Fx, Fy, Fz);                // Eqs. 37-39
             const Slot s = ad.src(k, ex, ey, ez);
             if (is16<T>() && k == 0) st.rest[3 * P.plane + s.node] = float(v);
             else Codec<T>::template store<SET_F>(element<T, 0>(st, k, s), v, D3Q19::w(k), P);
