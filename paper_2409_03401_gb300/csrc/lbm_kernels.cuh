@@ -525,23 +525,30 @@ __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, type
         // rest populations (natural units in every storage), stored last
         R g0, hA0, hB0;
         if constexpr (!is16<T>()) {
+            // The collisions keep sum g = phi~ + S and sum h = c - c_0^eq at the node (Eqs.
+            // 47-48, 51 with the shifted h_0): each rest population takes that total minus the
+            // moving populations it stores. Rounding the 2 Q collided values independently
+            // instead leaves a node's sums off by a few units in the last place, the same at
+            // every node of a uniform region, which adds up to a drift of the lattice totals.
+            g0 = phi + R(0.5) * nd.S;                                     // phi~ + S
+            hA0 = nd.dcA;
+            hB0 = nd.dcB;
     #pragma unroll
-            for (int k = 0; k < Q; ++k) {
+            for (int k = 1; k < Q; ++k) {
                 const int ex = L::ex(k), ey = L::ey(k), ez = L::ez(k);
                 const R w = R(L::w(k));
                 const R cu = edot(ex, ey, ez, ux, uy, uz);
                 const R geq = w * (ga + gb * cu);
                 const R gpost = nd.g[k] - omg * (nd.g[k] - geq) + w * nd.S;
-                if (k == 0) {                                             // h_0 shifted by c_0^eq
-                    g0 = gpost;
-                    hA0 = nd.hA[0] - omA * (nd.hA[0] - (nd.dcA - (R(1) - w) * muA));
-                    hB0 = nd.hB[0] - omB * (nd.hB[0] - (nd.dcB - (R(1) - w) * muB));
-                    continue;
-                }
+                const R hApost = nd.hA[k] - omA * (nd.hA[k] - w * (muA + cAu * cu));
+                const R hBpost = nd.hB[k] - omB * (nd.hB[k] - w * (muB + cBu * cu));
                 const Slot s = ad.dst(k, ex, ey, ez);
                 *element<T, Planes<LAT>::G>(out, k, s) = gpost;
-                *element<T, Planes<LAT>::HA>(out, k, s) = nd.hA[k] - omA * (nd.hA[k] - w * (muA + cAu * cu));
-                *element<T, Planes<LAT>::HB>(out, k, s) = nd.hB[k] - omB * (nd.hB[k] - w * (muB + cBu * cu));
+                *element<T, Planes<LAT>::HA>(out, k, s) = hApost;
+                *element<T, Planes<LAT>::HB>(out, k, s) = hBpost;
+                g0 -= gpost;
+                hA0 -= hApost;
+                hB0 -= hBpost;
             }
         } else {
             // the collisions keep sum g = phi~ + S and sum h = c - c_0^eq (Eqs. 47-48, 51 with the
@@ -573,15 +580,11 @@ __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, type
         store_scalar<T, SET_H, LAT, Planes<LAT>::HA, 1>(out, 0, s0, hA0, P);
         store_scalar<T, SET_H, LAT, Planes<LAT>::HB, 2>(out, 0, s0, hB0, P);
     };
-    // MRT instances collide the scalar sets first: their populations are dead before the
-    // moment transform needs the registers
-    if constexpr (COLL == 2) {
-        collide_s();
-        collide_f();
-    } else {
-        collide_f();
-        collide_s();
-    }
+    // the scalar sets first: their populations are dead before the flow collision needs the
+    // registers (MRT: no spills; BGK with the compensated rest populations: 16,193 MLUPS at
+    // 512^3 against 14,798 with the flow collision first)
+    collide_s();
+    collide_f();
 }
 
 // ------------------------------------------------------------------------------------
