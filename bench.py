@@ -32,7 +32,7 @@ ALG_BYTES_PER_NODE = {"f32": 320.0, "f16": 176.0, "bf16": 176.0, "f64": 640.0}
 # DRAM bytes (read + write) per node of one fused_flow_kernel<float> launch, from an ncu capture
 # of this kernel at 192^3; traffic scales with the
 # node count. Set to None whenever the kernel changes until it is captured again.
-NCU_DRAM_BYTES_PER_NODE_F32 = 164.98 + 153.87
+NCU_DRAM_BYTES_PER_NODE_F32 = 164.05 + 153.90
 
 
 def parse():
@@ -351,6 +351,19 @@ def gb300(args):
         var["trt"] = {"value": ws * nodes * vs / (vms / 1e3) / 1e6, "unit": "MLUPS", "ms_per_step": vms / vs,
                       "speedup_vs_f32": (ms / args.steps) / (vms / vs), "collision": "TRT, Lambda = 3/16",
                       "roofline_frac": ALG_BYTES_PER_NODE["f32"] * nodes / (vstep / 1e3) / 1e9 / peak}
+        del v
+        torch.cuda.synchronize()
+        # the in-place layout (one AA-pattern copy: half the memory of the two-buffer fused
+        # kernel), FP32: a phi pass, then the per-node AA step reading phi from it
+        q = p.with_(inplace=True)
+        v = Simulation(q, *init, device=device)
+        vs = max(20, args.steps // 2)
+        vms, vphi, vstep = time_device(v, vs, args.warmup, dist)
+        var["inplace"] = {"value": ws * nodes * vs / (vms / 1e3) / 1e6, "unit": "MLUPS", "ms_per_step": vms / vs,
+                          "speedup_vs_f32": (ms / args.steps) / (vms / vs),
+                          "kernels": "phi_kernel + step_kernel (AA pattern, in place)",
+                          "phi_pass_ms": vphi, "step_kernel_ms": vstep, "state_gb": v.state.numel() / 1e9,
+                          "roofline_frac": ALG_BYTES_PER_NODE["f32"] * nodes / (vms / vs / 1e3) / 1e9 / peak}
         del v
         torch.cuda.synchronize()
         # the multiple-relaxation-time flow collision (D3Q19 moment basis), FP32 storage

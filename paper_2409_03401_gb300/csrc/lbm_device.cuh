@@ -235,27 +235,33 @@ __device__ __forceinline__ unsigned short q15_enc(float v) {
 constexpr float kF16FScale = 1024.0f;  // Store16 f: IEEE FP16 of 1024 x
 constexpr float kF16HScale = 64.0f;  // Store16 h: IEEE FP16 of 64 x (x ~ mu stays clear of subnormals)
 
+// Each set is stored in units of r = unit * x (unit: f 1024, g 1, h 64 for Store16; 1 for
+// BF16); dec returns r, enc takes r.
 template <class H> struct Codec16;
 template <> struct Codec16<Store16> {
+    template <int SET> __host__ __device__ static constexpr float unit() {
+        return SET == SET_F ? kF16FScale : (SET == SET_H ? kF16HScale : 1.0f);
+    }
     template <int SET> __device__ static float dec(Store16 v) {
         if (SET == SET_G) return fmt16::q15_dec(v.bits);
-        if (SET == SET_F) return __half2float(__ushort_as_half(v.bits)) * (1.0f / kF16FScale);
-        return __half2float(__ushort_as_half(v.bits)) * (1.0f / kF16HScale);
+        return __half2float(__ushort_as_half(v.bits));
     }
-    template <int SET> __device__ static Store16 enc(float x) {
-        if (SET == SET_G) return Store16{fmt16::q15_enc(x)};
-        if (SET == SET_F) return Store16{__half_as_ushort(__float2half_rn(x * kF16FScale))};
-        return Store16{__half_as_ushort(__float2half_rn(x * kF16HScale))};
+    template <int SET> __device__ static Store16 enc(float r) {
+        if (SET == SET_G) return Store16{fmt16::q15_enc(r)};
+        return Store16{__half_as_ushort(__float2half_rn(r))};
     }
 };
 template <> struct Codec16<__nv_bfloat16> {
+    template <int SET> __host__ __device__ static constexpr float unit() { return 1.0f; }
     template <int SET> __device__ static float dec(__nv_bfloat16 v) { return __bfloat162float(v); }
-    template <int SET> __device__ static __nv_bfloat16 enc(float x) { return __float2bfloat16_rn(x); }
+    template <int SET> __device__ static __nv_bfloat16 enc(float r) { return __float2bfloat16_rn(r); }
 };
 
-// The per-unit-weight codec behind the node loaders: population = scale * x + offset.
+// The codec behind the node loaders: population = scale * r + offset, r as stored.
 template <class H> struct Codec16Pop : Codec16<H> {
-    template <int SET> __host__ __device__ static constexpr double scale(double w) { return w; }
+    template <int SET> __host__ __device__ static constexpr double scale(double w) {
+        return w / Codec16<H>::template unit<SET>();
+    }
     template <int SET> __host__ __device__ static constexpr double offset(double w) {
         return SET == SET_G ? 0.5 * w : 0.0;
     }
@@ -264,15 +270,16 @@ template <class H> struct Codec16Pop : Codec16<H> {
     // encode a population given in natural units (initial state; f with a zero reference)
     template <int SET>
     __device__ static void store(H* p, float v, double w, const DevParams&) {
-        const float x = SET == SET_G ? v * float(1.0 / w) - 0.5f : v * float(1.0 / w);
-        *p = Codec16<H>::template enc<SET>(x);
+        constexpr float u = Codec16<H>::template unit<SET>();
+        const float r = SET == SET_G ? v * float(u / w) - 0.5f * u : v * float(u / w);
+        *p = Codec16<H>::template enc<SET>(r);
     }
-    // Store x and return the value as stored, dec(enc(x)): the caller subtracts the moving
+    // Store r and return the value as stored, dec(enc(r)): the caller subtracts the moving
     // populations as stored from the node's conserved total to set the FP32 rest population
     // of g and h, so 16-bit rounding never changes those sums.
     template <int SET>
-    __device__ static float store_back(H* p, float x) {
-        const H h = Codec16<H>::template enc<SET>(x);
+    __device__ static float store_back(H* p, float r) {
+        const H h = Codec16<H>::template enc<SET>(r);
         *p = h;
         return Codec16<H>::template dec<SET>(h);
     }

@@ -145,8 +145,9 @@ struct Node {
             hB[k] = load_scalar<T, SET_H, LAT, Planes<LAT>::HB, 2>(st, k, s, P);
         }
     }
-    // With 16-bit storage ``ref(k, ex, ey, ez, slot)`` gives the FP32 f_0 of the node that
-    // stored the population gathered as k (for k = 0 the node's own f_0).
+    // With 16-bit storage ``ref(k, ex, ey, ez, slot)`` gives f_0 / w_0 of the node that stored
+    // the population gathered as k (for k = 0 of the node itself), and f_k / w_k is the stored
+    // deviation, in its storage unit, plus that reference (Codec16Pop).
     template <class A, class Ref>
     __device__ __forceinline__ void gather_flow(const StateView& st, const A& ad, const DevParams& P, Ref ref) {
         if constexpr (FLOW) {
@@ -155,10 +156,9 @@ struct Node {
                 const int ex = D3Q19::ex(k), ey = D3Q19::ey(k), ez = D3Q19::ez(k);
                 const Slot s = ad.src(k, ex, ey, ez);
                 if constexpr (is16<T>()) {
-                    // f_k / w_k = stored deviation + the writer's f_0 / w_0 (Codec16Pop)
-                    if (k == 0) f[0] = ref(0, 0, 0, 0, s);
-                    else f[k] = fmaf(ref(k, ex, ey, ez, s), float(1.0 / D3Q19::w(0)),
-                                     Codec<T>::template load<SET_F>(element<T, 0>(st, k, s), D3Q19::w(k), P));
+                    if (k == 0) f[0] = R(D3Q19::w(0)) * ref(0, 0, 0, 0, s);
+                    else f[k] = fmaf(Codec<T>::template load<SET_F>(element<T, 0>(st, k, s), D3Q19::w(k), P),
+                                     1.0f / Codec<T>::template unit<SET_F>(), ref(k, ex, ey, ez, s));
                 } else {
                     f[k] = Codec<T>::template load<SET_F>(element<T, 0>(st, k, s), D3Q19::w(k), P);
                 }
@@ -168,7 +168,9 @@ struct Node {
     template <class A>
     __device__ __forceinline__ void gather_flow(const StateView& st, const A& ad, const DevParams& P) {
         const float* f0 = is16<T>() ? st.rest + A::kF0In * P.plane : nullptr;
-        gather_flow(st, ad, P, [&](int k, int ex, int ey, int ez, Slot) { return f0[ad.writer(k, ex, ey, ez)]; });
+        gather_flow(st, ad, P, [&](int k, int ex, int ey, int ez, Slot) {
+            return f0[ad.writer(k, ex, ey, ez)] * float(1.0 / D3Q19::w(0));
+        });
     }
     template <class A>
     __device__ __forceinline__ void gather(const StateView& st, const A& ad, const DevParams& P) {
@@ -220,9 +222,9 @@ struct Node {
     __device__ __forceinline__ R flow_p() const {
         static_assert(FLOW, "flow moments of a node without flow populations");
         if constexpr (is16<T>()) {
-            R ph = f[0];
+            R ph = f[0];                                    // f_k / w_k for k > 0
 #pragma unroll
-            for (int k = 1; k < 19; ++k) ph += R(Codec<T>::template scale<SET_F>(D3Q19::w(k))) * f[k];
+            for (int k = 1; k < 19; ++k) ph += R(D3Q19::w(k)) * f[k];
             return ph;
         } else {
             R ph = R(0);
@@ -238,7 +240,7 @@ struct Node {
 #pragma unroll
         for (int k = 1; k < 19; ++k) {
             R v = f[k];
-            if constexpr (is16<T>()) v *= R(Codec<T>::template scale<SET_F>(D3Q19::w(k)));
+            if constexpr (is16<T>()) v *= R(D3Q19::w(k));   // f_k / w_k
             if (D3Q19::ex(k)) jx += R(D3Q19::ex(k)) * v;
             if (D3Q19::ey(k)) jy += R(D3Q19::ey(k)) * v;
             if (D3Q19::ez(k)) jz += R(D3Q19::ez(k)) * v;
@@ -452,15 +454,16 @@ __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, type
                 // w_k. f*_0 is stored first, in FP32, and is the reference of every moving
                 // population this node stores: x*_k - f*_0 / w_0 is what gets rounded.
                 using C = Codec<T>;
-                R ref = R(0);
+                constexpr float u = C::template unit<SET_F>();
+                R nref = R(0);                                    // -u f*_0 / w_0
                 auto put0 = [&](R f0post) {
                     const float f0s = float(f0post);
                     out.rest[A::kF0Out * P.plane + self] = f0s;
-                    ref = R(f0s) * R(1.0 / D3Q19::w(0));
+                    nref = R(f0s) * R(-u / D3Q19::w(0));
                 };
-                auto put = [&](int k, R x) {
+                auto put = [&](int k, R x) {                      // x = f*_k / w_k
                     const Slot sl = ad.dst(k, D3Q19::ex(k), D3Q19::ey(k), D3Q19::ez(k));
-                    *element<T, 0>(out, k, sl) = C::template enc<SET_F>(float(x - ref));
+                    *element<T, 0>(out, k, sl) = C::template enc<SET_F>(fmaf(float(x), u, float(nref)));
                 };
                 const R w0 = R(D3Q19::w(0));
                 const int coll = COLL >= 0 ? COLL : (COLL == -1 && P.coll == 2 ? 0 : P.coll);
@@ -556,12 +559,14 @@ __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, type
             g0 = phi + R(0.5) * nd.S - R(0.5 * (1.0 - L::w(0)));       // phi~ + S = phi + S/2
             hA0 = nd.dcA;
             hB0 = nd.dcB;
-            // per unit weight: g = w (x + 1/2) gives x* = x - om (x + 1/2 - ga - gb cu) + S, and
-            // h = w x gives x* = x - om (x - (mu + c cu / cs2))
+            // in storage units r = u x: g = w (x + 1/2) (u = 1) gives x* = x - om (x + 1/2 - ga -
+            // gb cu) + S, and h = (w / u) r gives r* = r - om (r - u (mu + c cu / cs2))
             using C = Codec<T>;
+            static_assert(C::template unit<SET_G>() == 1.0f, "g in units of x");
+            constexpr float uh = C::template unit<SET_H>();
             const R gq = R(0.5) - ga;
-            const R mA = muA, mB = muB;
-            const R cA = cAu, cB = cBu;
+            const R mA = R(uh) * muA, mB = R(uh) * muB;
+            const R cA = R(uh) * cAu, cB = R(uh) * cBu;
     #pragma unroll
             for (int k = 1; k < Q; ++k) {
                 const int ex = L::ex(k), ey = L::ey(k), ez = L::ez(k);
@@ -570,9 +575,12 @@ __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, type
                 const R qg = nd.g[k] - omg * (nd.g[k] + gq - gb * cu) + nd.S;
                 const R qA = nd.hA[k] - omA * (nd.hA[k] - (mA + cA * cu));
                 const R qB = nd.hB[k] - omB * (nd.hB[k] - (mB + cB * cu));
-                g0 -= R(L::w(k)) * C::template store_back<SET_G>(element<T, Planes<LAT>::G>(out, k, s), qg);
-                hA0 -= R(L::w(k)) * C::template store_back<SET_H>(element<T, Planes<LAT>::HA>(out, k, s), qA);
-                hB0 -= R(L::w(k)) * C::template store_back<SET_H>(element<T, Planes<LAT>::HB>(out, k, s), qB);
+                g0 -= R(C::template scale<SET_G>(L::w(k))) *
+                      C::template store_back<SET_G>(element<T, Planes<LAT>::G>(out, k, s), qg);
+                hA0 -= R(C::template scale<SET_H>(L::w(k))) *
+                       C::template store_back<SET_H>(element<T, Planes<LAT>::HA>(out, k, s), qA);
+                hB0 -= R(C::template scale<SET_H>(L::w(k))) *
+                       C::template store_back<SET_H>(element<T, Planes<LAT>::HB>(out, k, s), qB);
             }
         }
         const Slot s0{self, 0};
@@ -580,11 +588,18 @@ __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, type
         store_scalar<T, SET_H, LAT, Planes<LAT>::HA, 1>(out, 0, s0, hA0, P);
         store_scalar<T, SET_H, LAT, Planes<LAT>::HB, 2>(out, 0, s0, hB0, P);
     };
-    // the scalar sets first: their populations are dead before the flow collision needs the
+    // D3Q7 scalar sets first: their populations are dead before the flow collision needs the
     // registers (MRT: no spills; BGK with the compensated rest populations: 16,193 MLUPS at
-    // 512^3 against 14,798 with the flow collision first)
-    collide_s();
-    collide_f();
+    // 512^3 against 14,798 with the flow collision first). The 57 populations of D3Q19 scalar
+    // sets go after the flow's 19 (the per-node D3Q19 step ran at 6,037 against 7,783 MLUPS
+    // the other way round).
+    if constexpr (Q == 19) {
+        collide_f();
+        collide_s();
+    } else {
+        collide_s();
+        collide_f();
+    }
 }
 
 // ------------------------------------------------------------------------------------
@@ -704,7 +719,9 @@ fused_flow_kernel(const DevParams P, const StateView src, const StateView dst, i
     R (*ring)[FY + 2][FX + 2] = reinterpret_cast<R (*)[FY + 2][FX + 2]>(smem_raw);
     R* spops = reinterpret_cast<R*>(smem_raw) + 4 * (FY + 2) * (FX + 2);   // [2][spops_n][FT]
     constexpr int kSPops = spops_n<T>();
+    // f_0 / w_0 of the ring's positions (16-bit storage)
     float (*fring)[FY + 2][FX + 2] = reinterpret_cast<float (*)[FY + 2][FX + 2]>(spops + 2 * kSPops * FT);
+    constexpr float kInvW0 = float(1.0 / D3Q19::w(0));
     constexpr bool kParkDc = park_dc<T>();
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * FX + tx;
@@ -783,7 +800,7 @@ fused_flow_kernel(const DevParams P, const StateView src, const StateView dst, i
         }
         ring[s][ty + 1][tx + 1] = v;
         if constexpr (is16<T>())
-            fring[s][ty + 1][tx + 1] = own_ok ? src.rest[3 * P.plane + node_of(ox, oy, zr, P)] : 0.f;
+            fring[s][ty + 1][tx + 1] = own_ok ? src.rest[3 * P.plane + node_of(ox, oy, zr, P)] * kInvW0 : 0.f;
         if (tid < kHalo) {
             R hv = R(0);
             if (halo_ok) {
@@ -800,7 +817,7 @@ fused_flow_kernel(const DevParams P, const StateView src, const StateView dst, i
             }
             ring[s][hyp + 1][hxp + 1] = hv;
             if constexpr (is16<T>())
-                fring[s][hyp + 1][hxp + 1] = halo_ok ? src.rest[3 * P.plane + node_of(hgx, hgy, zr, P)] : 0.f;
+                fring[s][hyp + 1][hxp + 1] = halo_ok ? src.rest[3 * P.plane + node_of(hgx, hgy, zr, P)] * kInvW0 : 0.f;
         }
     };
 
@@ -813,8 +830,8 @@ fused_flow_kernel(const DevParams P, const StateView src, const StateView dst, i
         if (tid < kHalo) ring[s][hyp + 1][hxp + 1] = halo_ok ? gh[hgy * P.nx + hgx] : R(0);
         if constexpr (is16<T>()) {
             const float* f0 = src.rest + 3 * P.plane;
-            fring[s][ty + 1][tx + 1] = own_ok ? f0[node_of(ox, oy, zz, P)] : 0.f;
-            if (tid < kHalo) fring[s][hyp + 1][hxp + 1] = halo_ok ? f0[node_of(hgx, hgy, zz, P)] : 0.f;
+            fring[s][ty + 1][tx + 1] = own_ok ? f0[node_of(ox, oy, zz, P)] * kInvW0 : 0.f;
+            if (tid < kHalo) fring[s][hyp + 1][hxp + 1] = halo_ok ? f0[node_of(hgx, hgy, zz, P)] * kInvW0 : 0.f;
         }
     };
     auto fill_any = [&](int zz, int s, int buf) {
@@ -829,7 +846,7 @@ fused_flow_kernel(const DevParams P, const StateView src, const StateView dst, i
     auto centre = [&](const auto& ad, int z) {
         const int sp = (z - 1) & 3, sc = z & 3, sn = (z + 1) & 3;
         Node<T, LAT_D3Q7, true> nd;
-        // 16-bit storage: the writers' f_0 from the ring (the node itself across a wall)
+        // 16-bit storage: the writers' f_0 / w_0 from the ring (the node itself across a wall)
         nd.gather_flow(src, ad, P, [&](int k, int ex, int ey, int ez, Slot s) {
             if (k == 0 || s.node == ad.self) return fring[sc][ty + 1][tx + 1];
             return fring[ez > 0 ? sp : (ez < 0 ? sn : sc)][ty + 1 - ey][tx + 1 - ex];
