@@ -92,13 +92,14 @@ RIPENING_2D_M_PHI = (0.8776 - 0.5) / 3.0
 RIPENING_2D_R = (math.sqrt(26.5 / math.pi), math.sqrt(829.5 / math.pi))
 
 
-def ripening_2d(n=4096, storage="f32", shape=None, seed=6):
-    """2D Ostwald ripening without flow, periodic, on D2Q9 (the paper's 4096^2 run)."""
+def ripening_2d(n=4096, storage="f32", shape=None, seed=6, r_max=RIPENING_2D_R[1]):
+    """2D Ostwald ripening without flow, periodic, on D2Q9 (the paper's 4096^2 run). ``r_max``
+    caps the droplet radii (smaller boxes hold more, smaller droplets)."""
     nz, ny, nx = shape or (1, n, n)
     p = LBMParams(nx=nx, ny=ny, nz=nz, lattice="D2Q9", flow=False, storage=storage, W=3.0, lam=155.95,
                   M_phi=RIPENING_2D_M_PHI, c_eq=((0.3, 0.3), (0.4, 0.4)),
                   M=(RIPENING_2D_M, RIPENING_2D_M))
-    return p, _droplet_workload(p, 0.08, RIPENING_2D_R[0], RIPENING_2D_R[1], seed, sample_volume=True,
+    return p, _droplet_workload(p, 0.08, RIPENING_2D_R[0], r_max, seed, sample_volume=True,
                                 supersaturation=0.1)
 
 
