@@ -19,7 +19,8 @@ per snapshot, plus whole-lattice sums and the droplet count.
   (long_*_sensitivity.npz). Past step 5000 the test holds the invariants instead: the
   droplet count, and sum c^A, sum c^B within 1e-8.
 * Adjoint (32^3 ripening at 30 % supersaturation, 2,000 steps, checkpoints every 100 steps,
-  FP32 forward and reverse sweeps): misfit and gradient against the oracle's reverse mode.
+  FP32 forward and reverse sweeps): misfit, gradient w.r.t. (D_0, D_1, M_phi) and w.r.t.
+  phi_0 within the FP32 bar of 1e-5 of the oracle's reverse mode.
 """
 import os
 import sys
@@ -110,4 +111,4 @@ def test_adjoint_at_the_workload_horizon():
     e_phi = float((gphi.double().cpu() - gphi_ref).abs().max() / gphi_ref.abs().max())
     print(f"adjoint {c['shape']} x {steps}, K = {K}: L {L:.6e} (oracle {L_ref:.6e}), rel. errors L {e_L:.2e}, "
           f"theta {e_th:.2e}, phi0 {e_phi:.2e}")
-    assert e_L <= 1e-4 and e_th <= 1e-3 and e_phi <= 1e-2
+    assert max(e_L, e_th, e_phi) <= TOL["f32"]
