@@ -257,6 +257,13 @@ lbm_status lbm_adjoint_init(const lbm_params* p, const double* d_phi0, const dou
  * Synchronises the stream. */
 lbm_status lbm_adjoint_theta(const lbm_params* p, void* d_adj_work, double* out, void* stream);
 
+/* Mean droplet radius from the sums of lbm_reduce (or lbm_reduce_static): with A the
+ * interface measure (LBM_RED_INTERFACE, Eq. 67's sum of (4/W) phi (1 - phi)) and N the
+ * droplet count (LBM_RED_EULER), <R> = A / (2 pi N) on 2D lattices (Eq. 67) and
+ * sqrt(A / (4 pi N)) on 3D lattices (the sum of the sphere areas). NaN when N <= 0 or an
+ * argument is NULL. Host arithmetic only. */
+double lbm_mean_radius(const lbm_params* p, const double* sums);
+
 /* ------------------------------------------------------------------------------------
  * Slabs: a 3D lattice decomposed along z, the paper's domain decomposition for its
  * multi-GPU runs (§3; §4.2.4 ran 2048 x 512 x 512 on 64 GPUs). A slab owns the planes

@@ -94,6 +94,7 @@ def load():
         "lbm_slab_unpack": (ctypes.c_int, [vp, ctypes.c_int32, vp]),
         "lbm_slab_phi_pack": (ctypes.c_int, [vp, ctypes.c_int32, vp]),
         "lbm_slab_phi_unpack": (ctypes.c_int, [vp, ctypes.c_int32, vp]),
+        "lbm_mean_radius": (ctypes.c_double, [P, ctypes.POINTER(ctypes.c_double)]),
         "lbm_last_error": (ctypes.c_char_p, [vp]),
         "lbm_build_info": (ctypes.c_char_p, []),
     }
@@ -113,7 +114,8 @@ def exported_symbols():
             "lbm_adjoint_reset", "lbm_adjoint_seed", "lbm_adjoint_step", "lbm_adjoint_segment", "lbm_adjoint_init",
             "lbm_adjoint_theta", "lbm_reduce_static", "lbm_slab_planes", "lbm_slab_state_bytes",
             "lbm_slab_work_bytes", "lbm_slab_init", "lbm_slab_ghosts", "lbm_slab_halo_bytes", "lbm_slab_phi_bytes",
-            "lbm_slab_pack", "lbm_slab_unpack", "lbm_slab_phi_pack", "lbm_slab_phi_unpack", "lbm_destroy",
+            "lbm_slab_pack", "lbm_slab_unpack", "lbm_slab_phi_pack", "lbm_slab_phi_unpack", "lbm_mean_radius",
+            "lbm_destroy",
             "lbm_last_error", "lbm_build_info"]
 
 

@@ -1,4 +1,5 @@
 // C-ABI entry points (include/lbm.h): validation, buffer layout, launch sequencing.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -813,6 +814,14 @@ lbm_status lbm_destroy(lbm_ctx* c) {
 
 const char* lbm_last_error(const lbm_ctx* c) {
     return c ? c->err.c_str() : g_last_error.c_str();
+}
+
+double lbm_mean_radius(const lbm_params* p, const double* sums) {
+    if (!p || !sums) return NAN;
+    const double n = sums[LBM_RED_EULER], a = sums[LBM_RED_INTERFACE];
+    if (!(n > 0)) return NAN;
+    const double pi = 3.14159265358979323846;
+    return two_d(p->lattice) ? a / (2.0 * pi * n) : sqrt(a / (4.0 * pi * n));
 }
 
 const char* lbm_build_info(void) {

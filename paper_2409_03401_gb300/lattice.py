@@ -5,7 +5,6 @@ device, binds them with lbm_init, and forwards lbm_step / lbm_fields / lbm_reduc
 Every step of the method runs in the sm_103a kernels of liblbm_gb300.so.
 """
 import ctypes
-import math
 
 import torch
 
@@ -16,19 +15,15 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def droplet_stats(sums, two_d):
-    """Droplet count N (the Euler characteristic of the reduction) and mean radius <R> from
-    the interface measure A = sum (4/W) phi (1 - phi): <R> = A / (2 pi N) in 2D (Eq. 67),
-    sqrt(A / (4 pi N)) in 3D (sum of sphere areas). <R> is NaN when N <= 0."""
-    n = sums["euler"]
-    a = sums["interface"]
-    if n <= 0:
-        r = float("nan")
-    elif two_d:
-        r = a / (2.0 * math.pi * n)
-    else:
-        r = math.sqrt(a / (4.0 * math.pi * n))
-    return {"N": n, "R_mean": r, "interface": a}
+def droplet_stats(params, sums):
+    """Droplet count N (the Euler characteristic of the reduction) and mean radius <R>
+    (lbm_mean_radius: Eq. 67 in 2D, the sphere-area analogue in 3D) from a dict of lbm_reduce
+    sums. <R> is NaN when N <= 0."""
+    lib = _lib.load()
+    cp = _lib.make_params(params)
+    arr = (ctypes.c_double * _lib.NRED)(*[float(sums[k]) for k in _lib.REDUCTIONS])
+    return {"N": sums["euler"], "R_mean": lib.lbm_mean_radius(ctypes.byref(cp), arr),
+            "interface": sums["interface"]}
 
 
 class Simulation:
@@ -159,7 +154,7 @@ class Simulation:
     def droplets(self):
         """Droplet count N and mean radius <R> of the current time level (§4.2.2, one
         reduction pass on the device; synchronises the stream)."""
-        return droplet_stats(self.sums(), self.params.lattice in ("D2Q5", "D2Q9"))
+        return droplet_stats(self.params, self.sums())
 
     def profile_begin(self, max_steps):
         """Record CUDA events around this context's kernels for the next max_steps steps."""

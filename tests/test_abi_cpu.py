@@ -134,3 +134,23 @@ def test_adjoint_wrapper_rejects_bad_arguments_up_front(lib):
         CoupledRun.apply(phi, th, p.with_(storage="f16"), cA, cB, 10, 5)
     with pytest.raises(ValueError, match="without flow"):
         CoupledRun.apply(phi, th, p.with_(flow=True), cA, cB, 10, 5)
+
+
+def test_mean_radius_is_host_arithmetic(lib):
+    # <R> from the reduction sums (Eq. 67 in 2D, the sphere-area analogue in 3D): no device
+    import math
+    from paper_2409_03401_gb300 import _lib
+    from workloads.params import LBMParams
+    idx = {k: i for i, k in enumerate(_lib.REDUCTIONS)}
+    sums = (ctypes.c_double * _lib.NRED)()
+    sums[idx["interface"]] = 2 * math.pi * 5.0 * 7                  # seven discs of radius 5
+    sums[idx["euler"]] = 7
+    p2 = _lib.make_params(LBMParams(nx=64, ny=64, nz=1, lattice="D2Q9"))
+    assert lib.lbm_mean_radius(ctypes.byref(p2), sums) == pytest.approx(5.0)
+    sums[idx["interface"]] = 4 * math.pi * 6.0 ** 2 * 3              # three spheres of radius 6
+    sums[idx["euler"]] = 3
+    p3 = _lib.make_params(LBMParams(nx=32, ny=32, nz=32))
+    assert lib.lbm_mean_radius(ctypes.byref(p3), sums) == pytest.approx(6.0)
+    sums[idx["euler"]] = 0
+    assert math.isnan(lib.lbm_mean_radius(ctypes.byref(p3), sums))
+    assert math.isnan(lib.lbm_mean_radius(None, sums))
