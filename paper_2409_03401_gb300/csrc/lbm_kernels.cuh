@@ -403,6 +403,19 @@ __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, type
                 G = (Ac + cu * (R(3) + R(4.5) * cu)) * (edot(ex, ey, ez, Fx, Fy, Fz) - uF);
                 E = Bc + cu * (R(1) + R(1.5) * cu) - R(0.5) * G;
             };
+            // the same for the opposite pair (k, k + 1): e.u and e.F change sign, so the even
+            // parts (A + 4.5 cu^2, B + 1.5 cu^2) are shared
+            auto force_eq_pair = [&](int k, R& Ga, R& Ea, R& Gb, R& Eb) {
+                const int ex = D3Q19::ex(k), ey = D3Q19::ey(k), ez = D3Q19::ez(k);
+                const R cu = edot(ex, ey, ez, ux, uy, uz);
+                const R eF = edot(ex, ey, ez, Fx, Fy, Fz);
+                const R c2 = cu * cu;
+                const R Pe = Ac + R(4.5) * c2, Qe = Bc + R(1.5) * c2, t = R(3) * cu;
+                Ga = (Pe + t) * (eF - uF);
+                Gb = (t - Pe) * (eF + uF);
+                Ea = Qe + cu - R(0.5) * Ga;
+                Eb = Qe - cu - R(0.5) * Gb;
+            };
             if constexpr (!is16<T>()) {
                 auto put = [&](int k, R post) {
                     const Slot s = ad.dst(k, D3Q19::ex(k), D3Q19::ey(k), D3Q19::ez(k));
@@ -418,11 +431,16 @@ __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, type
                 };
                 const int coll = COLL >= 0 ? COLL : (COLL == -1 && P.coll == 2 ? 0 : P.coll);
                 if (coll == 0) {                                  // BGK, Eq. 36
+                    R F0, feq0;
+                    force_eq_w(0, F0, feq0);
+                    put(0, nd.f[0] - omf * (nd.f[0] - feq0) + F0);
     #pragma unroll
-                    for (int k = 0; k < 19; ++k) {
-                        R Fk, feq;
-                        force_eq_w(k, Fk, feq);
-                        put(k, nd.f[k] - omf * (nd.f[k] - feq) + Fk);
+                    for (int k = 1; k < 19; k += 2) {             // pairs (k, opp(k) = k + 1)
+                        const R w = R(D3Q19::w(k));
+                        R Ga, Ea, Gb, Eb;
+                        force_eq_pair(k, Ga, Ea, Gb, Eb);
+                        put(k, nd.f[k] - omf * (nd.f[k] - w * Ea) + w * Ga);
+                        put(k + 1, nd.f[k + 1] - omf * (nd.f[k + 1] - w * Eb) + w * Gb);
                     }
                 } else if ((COLL == 2 || COLL == -2) && coll == 2) {   // multiple relaxation times
                     R fF[19];                                  // f_k + F_k: f_k is dead after d_k
@@ -439,10 +457,11 @@ __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, type
                     put(0, nd.f[0] - omf * (nd.f[0] - feq0) + F0);
     #pragma unroll
                     for (int k = 1; k < 19; k += 2) {             // pairs (k, opp(k) = k + 1)
-                        R Fa, ea, Fb, eb;
-                        force_eq_w(k, Fa, ea);
-                        force_eq_w(k + 1, Fb, eb);
-                        const R da = nd.f[k] - ea, db = nd.f[k + 1] - eb;
+                        const R w = R(D3Q19::w(k));
+                        R Ga, Ea, Gb, Eb;
+                        force_eq_pair(k, Ga, Ea, Gb, Eb);
+                        const R Fa = w * Ga, Fb = w * Gb;
+                        const R da = nd.f[k] - w * Ea, db = nd.f[k + 1] - w * Eb;
                         const R even = R(0.5) * (da + db), odd = R(0.5) * (da - db);
                         put(k, nd.f[k] - omf * even - omm * odd + Fa);
                         put(k + 1, nd.f[k + 1] - omf * even + omm * odd + Fb);
@@ -490,18 +509,18 @@ __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, type
                     put0(nd.f[0] - omf * (nd.f[0] - w0 * E0) + w0 * G0);
                     if (coll == 0) {
     #pragma unroll
-                        for (int k = 1; k < 19; ++k) {
-                            R G, E;
-                            force_eq(k, G, E);
-                            put(k, nd.f[k] - omf * (nd.f[k] - E) + G);
+                        for (int k = 1; k < 19; k += 2) {
+                            R Ga, Ea, Gb, Eb;
+                            force_eq_pair(k, Ga, Ea, Gb, Eb);
+                            put(k, nd.f[k] - omf * (nd.f[k] - Ea) + Ga);
+                            put(k + 1, nd.f[k + 1] - omf * (nd.f[k + 1] - Eb) + Gb);
                         }
                     } else {
                         const R omm = coef<R>(P).om_fm;
     #pragma unroll
                         for (int k = 1; k < 19; k += 2) {
                             R Ga, Ea, Gb, Eb;
-                            force_eq(k, Ga, Ea);
-                            force_eq(k + 1, Gb, Eb);
+                            force_eq_pair(k, Ga, Ea, Gb, Eb);
                             const R da = nd.f[k] - Ea, db = nd.f[k + 1] - Eb;
                             const R even = R(0.5) * (da + db), odd = R(0.5) * (da - db);
                             put(k, nd.f[k] - omf * even - omm * odd + Ga);
