@@ -404,7 +404,9 @@ __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, type
                 E = Bc + cu * (R(1) + R(1.5) * cu) - R(0.5) * G;
             };
             // the same for the opposite pair (k, k + 1): e.u and e.F change sign, so the even
-            // parts (A + 4.5 cu^2, B + 1.5 cu^2) are shared
+            // parts (A + 4.5 cu^2, B + 1.5 cu^2) are shared (1 % faster for the D3Q7 fused kernel;
+            // the per-node D3Q19 step, at 128 registers, keeps one direction at a time for BGK:
+            // 7,519 against 6,507 MLUPS)
             auto force_eq_pair = [&](int k, R& Ga, R& Ea, R& Gb, R& Eb) {
                 const int ex = D3Q19::ex(k), ey = D3Q19::ey(k), ez = D3Q19::ez(k);
                 const R cu = edot(ex, ey, ez, ux, uy, uz);
@@ -430,7 +432,14 @@ __device__ __forceinline__ void collide_store(const Node<T, LAT, FLOW>& nd, type
                     feq = w * (Bc + cu * (R(1) + R(1.5) * cu)) - R(0.5) * Fk;
                 };
                 const int coll = COLL >= 0 ? COLL : (COLL == -1 && P.coll == 2 ? 0 : P.coll);
-                if (coll == 0) {                                  // BGK, Eq. 36
+                if (coll == 0 && Q == 19) {                       // BGK, Eq. 36 (see kPairs)
+    #pragma unroll
+                    for (int k = 0; k < 19; ++k) {
+                        R Fk, feq;
+                        force_eq_w(k, Fk, feq);
+                        put(k, nd.f[k] - omf * (nd.f[k] - feq) + Fk);
+                    }
+                } else if (coll == 0) {                           // BGK, Eq. 36
                     R F0, feq0;
                     force_eq_w(0, F0, feq0);
                     put(0, nd.f[0] - omf * (nd.f[0] - feq0) + F0);
