@@ -143,7 +143,7 @@ class Slab:
         return {k: out[i] for i, k in enumerate(_lib.REDUCTIONS)}
 
 
-def exchange_round(slabs, transport, pack, unpack, flow):
+def exchange_round(slabs, transport, pack, unpack):
     """Send every slab's face messages to its neighbours and unpack what arrives.
     ``slabs``: the slabs this process holds, keyed by slab index."""
     out = {i: {side: pack(s, side) for side in (0, 1) if s.has[side]} for i, s in slabs.items()}
@@ -156,9 +156,9 @@ def exchange_round(slabs, transport, pack, unpack, flow):
 def halo_exchange(slabs, transport, flow, populations=True):
     """Phases 2 and 3 of a step (phase 3 alone after initialisation)."""
     if populations:
-        exchange_round(slabs, transport, lambda s, d: s.pack(d), lambda s, d, m: s.unpack(d, m), flow)
+        exchange_round(slabs, transport, lambda s, d: s.pack(d), lambda s, d, m: s.unpack(d, m))
     if flow:
-        exchange_round(slabs, transport, lambda s, d: s.phi_pack(d), lambda s, d, m: s.phi_unpack(d, m), flow)
+        exchange_round(slabs, transport, lambda s, d: s.phi_pack(d), lambda s, d, m: s.phi_unpack(d, m))
 
 
 class LocalTransport:
