@@ -54,6 +54,9 @@ def parse():
                     help="instead of the bench: <R>^3 against t on the 256^3 (3D) and 4096^2 (2D) ripening runs")
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                     help="population storage of the main line (profiling runs; the headline is f32)")
+    ap.add_argument("--slabs", default="", metavar="N[,N...]",
+                    help="instead of the bench: the 512^3 FP32 step split into N z slabs on this GPU "
+                         "(halo exchange by device copies), against the undivided lattice")
     ap.add_argument("--adjoint-steps", type=int, default=200)
     ap.add_argument("--adjoint-k", type=int, default=100, help="checkpoint interval of the adjoint variant")
     return ap.parse_args()
@@ -561,9 +564,54 @@ def ripening_law(args):
     print(json.dumps(out))
 
 
+def slab_study(args):
+    """Cost of the z-slab decomposition on one GPU: the same workload as the bench, advanced
+    by a SlabGroup of N slabs (after every step each slab packs the populations leaving its
+    faces, the neighbours unpack them, then phi of the edge planes goes the same way), timed
+    with CUDA events around the steps and exchanges, against the undivided lattice."""
+    import torch
+    from paper_2409_03401_gb300 import Simulation
+    from paper_2409_03401_gb300.slabs import SlabGroup
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    p, _, init = make_workload(args.n, device, "f32")
+    steps = max(10, args.steps // 4)
+
+    def timed(obj):
+        obj.step(args.warmup)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        obj.step(steps)
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / steps
+
+    sim = Simulation(p, *init, device=device)
+    ms0 = timed(sim)
+    ref = sim.fields(("phi", "ux"))
+    t_ref = sim.t
+    del sim
+    torch.cuda.synchronize()
+    out = {"study": "slabs", "workload": f"{args.n}^3 FP32 flow (the bench workload), {steps} timed steps",
+           "undivided_ms_per_step": ms0, "undivided_mlups": p.nodes / (ms0 / 1e3) / 1e6, "runs": {}}
+    for n in [int(v) for v in args.slabs.split(",") if v]:
+        grp = SlabGroup(p, n, *init)
+        ms = timed(grp)
+        same = grp.t == t_ref and all(torch.equal(grp.fields((k,))[k], ref[k]) for k in ref)
+        out["runs"][str(n)] = {"ms_per_step": ms, "mlups": p.nodes / (ms / 1e3) / 1e6,
+                               "overhead_vs_undivided": ms / ms0 - 1.0, "halo_bytes_per_face": grp.slabs[0].halo_bytes,
+                               "fields_equal_to_undivided": bool(same)}
+        del grp
+        torch.cuda.synchronize()
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
-    if args.drift:
+    if args.slabs:
+        slab_study(args)
+    elif args.drift:
         drift_study(args)
     elif args.ripening_law:
         ripening_law(args)
