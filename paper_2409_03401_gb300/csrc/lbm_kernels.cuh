@@ -1016,9 +1016,9 @@ template <int LAT> constexpr bool kTwoD = LAT == LAT_D2Q5 || LAT == LAT_D2Q9;
 // quads: over all 2x2 windows, chi = (n1 - n3 - 2 nd) / 4 with n1 (n3) the windows holding
 // one (three) set pixels and nd those holding a diagonal pair. Node (x, y) owns the window
 // spanning x..x+1, y..y+1 (periodic wrap; outside an x wall counts as empty, and the node
-// at x = 0 also owns the window reaching out to x = -1). Returns its share of chi.
+// at x = 0 also owns the window reaching out to x = -1). Returns 4 times its share of chi.
 template <class R>
-__device__ __forceinline__ double euler_quads(const R* __restrict__ phi, int x, int y, const DevParams& P) {
+__device__ __forceinline__ int euler_quads4(const R* __restrict__ phi, int x, int y, const DevParams& P) {
     const int yp = y + 1 < P.ny ? y + 1 : 0;
     auto on = [&](int xx, int yy) {
         return xx >= 0 && xx < P.nx && phi[yy * P.nx + xx] >= R(0.5);
@@ -1027,12 +1027,12 @@ __device__ __forceinline__ double euler_quads(const R* __restrict__ phi, int x, 
         const int a = on(x0, y), b = on(x1, y), c = on(x0, yp), d = on(x1, yp);
         const int n = a + b + c + d;
         const int diag = (n == 2 && a == d) ? 1 : 0;
-        return double((n == 1) - (n == 3) - 2 * diag);
+        return int(n == 1) - int(n == 3) - 2 * diag;
     };
     const int xp = x + 1 < P.nx ? x + 1 : (P.wall_x ? P.nx : 0);
-    double q = window(x, xp);
+    int q = window(x, xp);
     if (P.wall_x && x == 0) q += window(-1, 0);
-    return 0.25 * q;
+    return q;
 }
 
 // Euler characteristic of the 26-connected set {phi >= 1/2} of a 3D lattice: the alternating
@@ -1059,7 +1059,7 @@ __device__ __forceinline__ int euler_cells(const unsigned* __restrict__ bits, in
                 if (yy < 0) yy += P.ny;
                 if (zz < 0) { inside = inside && !P.wall_z; zz += P.nz; }
                 if (zz >= P.nz) { inside = inside && !P.wall_z; zz -= P.nz; }
-                const long long id = ((long long)zz * P.ny + yy) * P.nx + xx;
+                const unsigned id = (unsigned(zz) * unsigned(P.ny) + unsigned(yy)) * unsigned(P.nx) + unsigned(xx);
                 b[c][bb][a] = inside ? int((__ldg(bits + (id >> 5)) >> (id & 31)) & 1u) : 0;
             }
     const int vert = b[0][0][0] | b[0][0][1] | b[0][1][0] | b[0][1][1] | b[1][0][0] | b[1][0][1] | b[1][1][0] |
@@ -1080,11 +1080,12 @@ template <class T>
 __global__ void __launch_bounds__(256)
 euler3d_kernel(const DevParams P, const unsigned* __restrict__ bits, double* __restrict__ partials) {
     long long acc = 0;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < P.n; id += stride) {
-        const int x = int(id % P.nx);
-        const int y = int((id / P.nx) % P.ny);
-        const int z = int(id / ((long long)P.nx * P.ny));
+    const unsigned stride = gridDim.x * blockDim.x;
+    const unsigned nxy = unsigned(P.nx) * unsigned(P.ny), n = unsigned(P.n);
+    for (unsigned id = blockIdx.x * blockDim.x + threadIdx.x; id < n; id += stride) {
+        const unsigned zu = id / nxy, xy = id - zu * nxy;
+        const unsigned yu = xy / unsigned(P.nx);
+        const int x = int(xy - yu * unsigned(P.nx)), y = int(yu), z = int(zu);
         const int x1 = (P.wall_x && x == P.nx - 1) ? P.nx : x;
         const int z1 = (P.wall_z && z == P.nz - 1) ? P.nz : z;
         for (int zs = z; zs <= z1; ++zs)
@@ -1102,55 +1103,82 @@ euler3d_kernel(const DevParams P, const unsigned* __restrict__ bits, double* __r
     }
 }
 
+// Running sum of one thread in the reduction. FP64 storage sums in FP64. With FP32 arithmetic
+// the sum is kept as an unevaluated pair hi + lo of FP32 numbers: TwoSum (Knuth, TAOCP vol. 2,
+// §4.2.2) returns the exact rounding error of each addition, which lo collects, so a thread's
+// few hundred terms lose nothing at FP64's level while every operation stays on the FP32
+// pipes (this part's FP64 rate is a small fraction of its FP32 rate).
+template <class R> struct SumAcc {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double v) { s += v; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct SumAcc<float> {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add(float v) {
+        const float s = hi + v;
+        const float bv = s - hi;
+        lo += (hi - (s - bv)) + (v - bv);
+        hi = s;
+    }
+    __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
+};
+
 // FP64 block partials of the global diagnostics (grid-stride over nodes; the 32 nodes a warp
 // visits together are consecutive and start at a multiple of 32). On 3D lattices it also
 // writes the bit field of phi >= 1/2 that euler3d_kernel reads, one warp vote per word.
+// Node indices are 32-bit (the host rejects lattices of 2^31 nodes or more). Per-node values
+// are formed in the kernels' arithmetic type and summed per thread (SumAcc); the c sums add
+// c_0^eq once per node counted, and the thread and block totals are combined in FP64.
 template <class T, int LAT, bool FLOW, int MODE>
 __global__ void __launch_bounds__(256)
 reduce_kernel(const DevParams P, const StateView st, const typename RealOf<T>::type* __restrict__ phi_field,
               unsigned* __restrict__ bits, double* __restrict__ partials) {
     using R = typename RealOf<T>::type;
-    double acc[LBM_NRED_DEV];
-#pragma unroll
-    for (int i = 0; i < LBM_NRED_DEV; ++i) acc[i] = 0.0;
+    SumAcc<R> s_phi, s_dcA, s_dcB, s_p, s_S, s_phit, s_int;
+    R umax = R(0);
+    int nodes = 0, bad = 0, quads = 0;
+    const R kint = R(4.0 / P.W);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long stride = (long long)gridDim.x * blockDim.x;
+    const unsigned nxy = unsigned(P.nx) * unsigned(P.ny);
+    const unsigned stride = gridDim.x * blockDim.x;
     // nodes of the planes [z_lo, z_hi); the bit field (3D Euler count) only when they start at 0
-    const long long id0 = (long long)P.z_lo * P.nx * P.ny, id1 = (long long)P.z_hi * P.nx * P.ny;
-    for (long long base = id0 + (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < id1; base += stride) {
-        const long long id = base + lane;
+    const unsigned id0 = unsigned(P.z_lo) * nxy, id1 = unsigned(P.z_hi) * nxy;
+    for (unsigned base = id0 + blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < id1; base += stride) {
+        const unsigned id = base + lane;
         bool on = false;
         if (id < id1) {
-            const int x = int(id % P.nx);
-            const int y = int((id / P.nx) % P.ny);
-            const int z = int(id / ((long long)P.nx * P.ny));
+            const unsigned z = id / nxy, xy = id - z * nxy;
+            const unsigned y = xy / unsigned(P.nx), x = xy - y * unsigned(P.nx);
             Addr<MODE> ad;
             ad.self = int(id);
-            ad.nb.init(x, y, z, P);
+            ad.nb.init(int(x), int(y), int(z), P);
             Node<T, LAT, FLOW> nd;
             nd.gather(st, ad, P);
             nd.moments(P);
             R phi;
             if constexpr (FLOW) phi = phi_field[id]; else phi = nd.phi();
-            double umag = 0.0, ph = 0.0;
+            R umag = R(0), ph = R(0);
             if constexpr (FLOW) {
                 R gx, gy, gz, lap, Fx, Fy, Fz, ux, uy, uz;
                 stencil([&](int dx, int dy, int dz) { return ad.phi(phi_field, dx, dy, dz); }, phi, gx, gy, gz, lap);
                 force_velocity(nd, phi, gx, gy, gz, lap, P, Fx, Fy, Fz, ux, uy, uz);
-                umag = sqrt(double(ux) * ux + double(uy) * uy + double(uz) * uz);
+                umag = sqrt(ux * ux + uy * uy + uz * uz);
                 ph = nd.flow_p();
             }
-            const double vals[5] = {double(phi), double(nd.dcA) + P.c0[0], double(nd.dcB) + P.c0[1], ph,
-                                    double(nd.S)};
-            bool finite = true;
-#pragma unroll
-            for (int i = 0; i < 5; ++i) { acc[i] += vals[i]; finite = finite && isfinite(vals[i]); }
-            finite = finite && isfinite(umag) && isfinite(double(nd.phit));
-            acc[5] = fmax(acc[5], isfinite(umag) ? umag : 0.0);
-            acc[6] += double(nd.phit);
-            acc[7] += finite ? 0.0 : 1.0;
-            acc[8] += 4.0 / P.W * double(phi) * (1.0 - double(phi));          // Eq. 67 integrand
-            if constexpr (kTwoD<LAT>) acc[9] += euler_quads(phi_field, x, y, P);
+            s_phi.add(phi);
+            s_dcA.add(nd.dcA);
+            s_dcB.add(nd.dcB);
+            s_p.add(ph);
+            s_S.add(nd.S);
+            s_phit.add(nd.phit);
+            s_int.add(kint * phi * (R(1) - phi));                        // Eq. 67 integrand
+            ++nodes;
+            const bool finite = isfinite(phi) && isfinite(nd.dcA) && isfinite(nd.dcB) && isfinite(ph) &&
+                                isfinite(nd.S) && isfinite(umag) && isfinite(nd.phit);
+            bad += finite ? 0 : 1;
+            if (isfinite(umag)) umax = umag > umax ? umag : umax;
+            if constexpr (kTwoD<LAT>) quads += euler_quads4(phi_field, int(x), int(y), P);
             on = phi >= R(0.5);
         }
         if constexpr (!kTwoD<LAT>) {
@@ -1160,6 +1188,17 @@ reduce_kernel(const DevParams P, const StateView st, const typename RealOf<T>::t
             }
         }
     }
+    double acc[LBM_NRED_DEV];
+    acc[0] = s_phi.value();
+    acc[1] = s_dcA.value() + double(nodes) * P.c0[0];
+    acc[2] = s_dcB.value() + double(nodes) * P.c0[1];
+    acc[3] = s_p.value();
+    acc[4] = s_S.value();
+    acc[5] = double(umax);
+    acc[6] = s_phit.value();
+    acc[7] = double(bad);
+    acc[8] = s_int.value();
+    acc[9] = 0.25 * double(quads);
     // block reduction: warp shuffles, then one warp over the warp results
     __shared__ double sm[LBM_NRED_DEV][32];
 #pragma unroll
@@ -1284,6 +1323,22 @@ struct Launchers {
         if constexpr (FLOW) { LBM_MODE_SWITCH(mode, phi_kernel<T, LAT, M><<<grid, bx, 0, s>>>(P, st, phi)); }
         LBM_MODE_SWITCH(mode, fields_kernel<T, LAT, FLOW, M><<<grid, bx, 0, s>>>(P, st, phi, out));
     }
+    // Blocks of 256 threads of ``kernel`` that the device holds at once, at most ``cap``: a
+    // grid-stride kernel launched with more would run its last blocks in a partial wave.
+    template <class K>
+    static int resident_blocks(K kernel, int cap) {
+        int dev = 0, sms = 0, per_sm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0) != cudaSuccess) {
+            cudaGetLastError();
+            return cap;
+        }
+        const long long n = (long long)per_sm * sms;
+        return (n > 0 && n < cap) ? int(n) : cap;
+    }
+    // Fills ``nblocks`` block partials: the grid-stride kernels run with the blocks the device
+    // holds at once and the partials of the blocks beyond are zeroed.
     template <int LAT, bool FLOW>
     static void reduce(const DevParams& P, const StateView& st, int mode, void* phi_work, void* bits_work,
                        double* partials, int nblocks, cudaStream_t s) {
@@ -1293,10 +1348,17 @@ struct Launchers {
             int bx; const dim3 grid = node_grid(P, bx);
             LBM_MODE_SWITCH(mode, phi_kernel<T, LAT, M><<<grid, bx, 0, s>>>(P, st, phi));
         }
-        LBM_MODE_SWITCH(mode, reduce_kernel<T, LAT, FLOW, M><<<nblocks, 256, 0, s>>>(P, st, phi, bits, partials));
+        int nb = nblocks;
+        LBM_MODE_SWITCH(mode, {
+            nb = resident_blocks(reduce_kernel<T, LAT, FLOW, M>, nblocks);
+            reduce_kernel<T, LAT, FLOW, M><<<nb, 256, 0, s>>>(P, st, phi, bits, partials);
+        });
+        if (nb < nblocks)
+            cudaMemsetAsync(partials + (size_t)nb * LBM_NRED_DEV, 0, (size_t)(nblocks - nb) * LBM_NRED_DEV * sizeof(double),
+                            s);
         // the 3D Euler count needs the bit field of the whole lattice (not kept for a slab)
         if constexpr (!kTwoD<LAT>) {
-            if (bits) euler3d_kernel<T><<<nblocks, 256, 0, s>>>(P, bits, partials);
+            if (bits) euler3d_kernel<T><<<resident_blocks(euler3d_kernel<T>, nblocks), 256, 0, s>>>(P, bits, partials);
         }
     }
 };
