@@ -165,9 +165,14 @@ def test_droplet_stats_of_the_binding_match_the_oracle(dims):
         shape = (1, 96, 110)
         centres, radii = place_droplets(shape, 0.1, 4.0, 9.0, W, seed=5)
     phi = phi_field(shape, centres, radii, W).numpy()
-    sums = {"euler": float(measure.euler_characteristic(phi)), "interface": measure.interface_measure(phi, W)}
-    got = droplet_stats(sums, two_d=(dims == 2))
+    from paper_2409_03401_gb300 import _lib
+    from workloads import configs
+    params = (configs.ripening_2d if dims == 2 else configs.ripening)(shape=shape)[0]
+    sums = dict.fromkeys(_lib.REDUCTIONS, 0.0)
+    sums.update(euler=float(measure.euler_characteristic(phi)), interface=measure.interface_measure(phi, W))
+    got = droplet_stats(params, sums)
     R, n = measure.mean_radius(phi, W)
     assert got["N"] == n == len(radii)
     assert abs(got["R_mean"] - R) < 1e-12 * R
-    assert math.isnan(droplet_stats({"euler": 0.0, "interface": 1.0}, two_d=False)["R_mean"])
+    sums.update(euler=0.0, interface=1.0)
+    assert math.isnan(droplet_stats(params, sums)["R_mean"])
