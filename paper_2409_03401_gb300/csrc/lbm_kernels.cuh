@@ -1105,13 +1105,17 @@ euler3d_kernel(const DevParams P, const unsigned* __restrict__ bits, double* __r
 
 // Running sum of one thread in the reduction. FP64 storage sums in FP64. With FP32 arithmetic
 // the sum is kept as an unevaluated pair hi + lo of FP32 numbers: TwoSum (Knuth, TAOCP vol. 2,
-// §4.2.2) returns the exact rounding error of each addition, which lo collects, so a thread's
-// few hundred terms lose nothing at FP64's level while every operation stays on the FP32
-// pipes (this part's FP64 rate is a small fraction of its FP32 rate).
+// §4.2.2) returns the exact rounding error of each addition, which lo collects, and every
+// kFlush terms the kernel moves the pair (take) into an FP64 total in shared memory. After m
+// terms the pair is off by at most m^2 2^-48 of its largest partial sum (lo's own roundings),
+// i.e. below 4e-12 relative for m = kFlush = 32, so the sums keep FP64-level accuracy while
+// the per-node work stays on the FP32 pipes (this part's FP64 rate is a small fraction of its
+// FP32 rate) and the FP64 totals take no registers.
+constexpr int kFlush = 32;
 template <class R> struct SumAcc {
     double s = 0.0;
     __device__ __forceinline__ void add(double v) { s += v; }
-    __device__ __forceinline__ double value() const { return s; }
+    __device__ __forceinline__ double take() { const double v = s; s = 0.0; return v; }
 };
 template <> struct SumAcc<float> {
     float hi = 0.0f, lo = 0.0f;
@@ -1121,7 +1125,11 @@ template <> struct SumAcc<float> {
         lo += (hi - (s - bv)) + (v - bv);
         hi = s;
     }
-    __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
+    __device__ __forceinline__ double take() {
+        const double v = double(hi) + double(lo);
+        hi = lo = 0.0f;
+        return v;
+    }
 };
 
 // FP64 block partials of the global diagnostics (grid-stride over nodes; the 32 nodes a warp
@@ -1130,12 +1138,27 @@ template <> struct SumAcc<float> {
 // Node indices are 32-bit (the host rejects lattices of 2^31 nodes or more). Per-node values
 // are formed in the kernels' arithmetic type and summed per thread (SumAcc); the c sums add
 // c_0^eq once per node counted, and the thread and block totals are combined in FP64.
+// blocks per SM the reduction's register budget is cut for: three (80 registers) with FP32
+// arithmetic, two (128) for FP64 values or the 57 scalar populations of D3Q19
+template <class T, int LAT> constexpr int reduce_min_blocks() {
+    return (LAT == LAT_D3Q19 || sizeof(typename RealOf<T>::type) == 8) ? 2 : 3;
+}
+
 template <class T, int LAT, bool FLOW, int MODE>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, (reduce_min_blocks<T, LAT>()))
 reduce_kernel(const DevParams P, const StateView st, const typename RealOf<T>::type* __restrict__ phi_field,
               unsigned* __restrict__ bits, double* __restrict__ partials) {
     using R = typename RealOf<T>::type;
+    constexpr int kSums = 7;
     SumAcc<R> s_phi, s_dcA, s_dcB, s_p, s_S, s_phit, s_int;
+    __shared__ double tot[kSums][256];                 // this thread's FP64 totals
+    auto flush = [&]() {
+        const int t = threadIdx.x;
+        tot[0][t] += s_phi.take(); tot[1][t] += s_dcA.take(); tot[2][t] += s_dcB.take();
+        tot[3][t] += s_p.take(); tot[4][t] += s_S.take(); tot[5][t] += s_phit.take(); tot[6][t] += s_int.take();
+    };
+#pragma unroll
+    for (int i = 0; i < kSums; ++i) tot[i][threadIdx.x] = 0.0;
     R umax = R(0);
     int nodes = 0, bad = 0, quads = 0;
     const R kint = R(4.0 / P.W);
@@ -1173,7 +1196,7 @@ reduce_kernel(const DevParams P, const StateView st, const typename RealOf<T>::t
             s_S.add(nd.S);
             s_phit.add(nd.phit);
             s_int.add(kint * phi * (R(1) - phi));                        // Eq. 67 integrand
-            ++nodes;
+            if (++nodes % kFlush == 0) flush();
             const bool finite = isfinite(phi) && isfinite(nd.dcA) && isfinite(nd.dcB) && isfinite(ph) &&
                                 isfinite(nd.S) && isfinite(umag) && isfinite(nd.phit);
             bad += finite ? 0 : 1;
@@ -1188,16 +1211,18 @@ reduce_kernel(const DevParams P, const StateView st, const typename RealOf<T>::t
             }
         }
     }
+    flush();
+    const int t = threadIdx.x;
     double acc[LBM_NRED_DEV];
-    acc[0] = s_phi.value();
-    acc[1] = s_dcA.value() + double(nodes) * P.c0[0];
-    acc[2] = s_dcB.value() + double(nodes) * P.c0[1];
-    acc[3] = s_p.value();
-    acc[4] = s_S.value();
+    acc[0] = tot[0][t];
+    acc[1] = tot[1][t] + double(nodes) * P.c0[0];
+    acc[2] = tot[2][t] + double(nodes) * P.c0[1];
+    acc[3] = tot[3][t];
+    acc[4] = tot[4][t];
     acc[5] = double(umax);
-    acc[6] = s_phit.value();
+    acc[6] = tot[5][t];
     acc[7] = double(bad);
-    acc[8] = s_int.value();
+    acc[8] = tot[6][t];
     acc[9] = 0.25 * double(quads);
     // block reduction: warp shuffles, then one warp over the warp results
     __shared__ double sm[LBM_NRED_DEV][32];
