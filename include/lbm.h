@@ -186,7 +186,7 @@ lbm_status lbm_fields(lbm_ctx* ctx, void* const* dst);
 /* FP64 global diagnostics of the current time level into host memory out[LBM_NRED]: the
  * sums of Eqs. 40, 49, 52, max |u| (§4.2.4), the interface measure of Eq. 67 and the droplet
  * count of §4.2.2 (LBM_RED_*). Per-node values are formed in the storage's arithmetic type
- * and summed with FP64 accuracy (compensated FP32 pairs per thread for FP32 arithmetic).
+ * and summed with FP64 accuracy (float-float FP32 pairs per thread for FP32 arithmetic).
  * Synchronises the stream. Returns LBM_ERR_UNSTABLE if a moment is not finite. */
 lbm_status lbm_reduce(lbm_ctx* ctx, double* out);
 

@@ -1104,32 +1104,29 @@ euler3d_kernel(const DevParams P, const unsigned* __restrict__ bits, double* __r
 }
 
 // Running sum of one thread in the reduction. FP64 storage sums in FP64. With FP32 arithmetic
-// the sum is kept as an unevaluated pair hi + lo of FP32 numbers: TwoSum (Knuth, TAOCP vol. 2,
-// §4.2.2) returns the exact rounding error of each addition, which lo collects, and every
-// kFlush terms the kernel moves the pair (take) into an FP64 total in shared memory. After m
-// terms the pair is off by at most m^2 2^-48 of its largest partial sum (lo's own roundings),
-// i.e. below 4e-12 relative for m = kFlush = 32, so the sums keep FP64-level accuracy while
-// the per-node work stays on the FP32 pipes (this part's FP64 rate is a small fraction of its
-// FP32 rate) and the FP64 totals take no registers.
-constexpr int kFlush = 32;
+// the sum is kept as an unevaluated pair hi + lo of FP32 numbers (float-float addition):
+// TwoSum (Knuth, TAOCP vol. 2, §4.2.2) gives the exact rounding error e of hi + v, e joins lo,
+// and FastTwoSum (Dekker 1971) renormalises the pair so that |lo| stays below half an ulp of
+// hi. Each addition then errs by at most about 2^-47 of the running sum, n terms by n 2^-47
+// (below 1e-11 relative for the ~1,200 nodes per thread of a 512^3 lattice), so the sums keep
+// FP64-level accuracy while the per-node work stays on the FP32 pipes (this part's FP64 rate
+// is a small fraction of its FP32 rate).
 template <class R> struct SumAcc {
     double s = 0.0;
     __device__ __forceinline__ void add(double v) { s += v; }
-    __device__ __forceinline__ double take() { const double v = s; s = 0.0; return v; }
+    __device__ __forceinline__ double value() const { return s; }
 };
 template <> struct SumAcc<float> {
     float hi = 0.0f, lo = 0.0f;
     __device__ __forceinline__ void add(float v) {
         const float s = hi + v;
         const float bv = s - hi;
-        lo += (hi - (s - bv)) + (v - bv);
-        hi = s;
+        const float e = (hi - (s - bv)) + (v - bv);
+        const float t = lo + e;
+        hi = s + t;
+        lo = t - (hi - s);
     }
-    __device__ __forceinline__ double take() {
-        const double v = double(hi) + double(lo);
-        hi = lo = 0.0f;
-        return v;
-    }
+    __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
 };
 
 // FP64 block partials of the global diagnostics (grid-stride over nodes; the 32 nodes a warp
@@ -1149,16 +1146,7 @@ __global__ void __launch_bounds__(256, (reduce_min_blocks<T, LAT>()))
 reduce_kernel(const DevParams P, const StateView st, const typename RealOf<T>::type* __restrict__ phi_field,
               unsigned* __restrict__ bits, double* __restrict__ partials) {
     using R = typename RealOf<T>::type;
-    constexpr int kSums = 7;
     SumAcc<R> s_phi, s_dcA, s_dcB, s_p, s_S, s_phit, s_int;
-    __shared__ double tot[kSums][256];                 // this thread's FP64 totals
-    auto flush = [&]() {
-        const int t = threadIdx.x;
-        tot[0][t] += s_phi.take(); tot[1][t] += s_dcA.take(); tot[2][t] += s_dcB.take();
-        tot[3][t] += s_p.take(); tot[4][t] += s_S.take(); tot[5][t] += s_phit.take(); tot[6][t] += s_int.take();
-    };
-#pragma unroll
-    for (int i = 0; i < kSums; ++i) tot[i][threadIdx.x] = 0.0;
     R umax = R(0);
     int nodes = 0, bad = 0, quads = 0;
     const R kint = R(4.0 / P.W);
@@ -1196,7 +1184,7 @@ reduce_kernel(const DevParams P, const StateView st, const typename RealOf<T>::t
             s_S.add(nd.S);
             s_phit.add(nd.phit);
             s_int.add(kint * phi * (R(1) - phi));                        // Eq. 67 integrand
-            if (++nodes % kFlush == 0) flush();
+            ++nodes;
             const bool finite = isfinite(phi) && isfinite(nd.dcA) && isfinite(nd.dcB) && isfinite(ph) &&
                                 isfinite(nd.S) && isfinite(umag) && isfinite(nd.phit);
             bad += finite ? 0 : 1;
@@ -1211,18 +1199,16 @@ reduce_kernel(const DevParams P, const StateView st, const typename RealOf<T>::t
             }
         }
     }
-    flush();
-    const int t = threadIdx.x;
     double acc[LBM_NRED_DEV];
-    acc[0] = tot[0][t];
-    acc[1] = tot[1][t] + double(nodes) * P.c0[0];
-    acc[2] = tot[2][t] + double(nodes) * P.c0[1];
-    acc[3] = tot[3][t];
-    acc[4] = tot[4][t];
+    acc[0] = s_phi.value();
+    acc[1] = s_dcA.value() + double(nodes) * P.c0[0];
+    acc[2] = s_dcB.value() + double(nodes) * P.c0[1];
+    acc[3] = s_p.value();
+    acc[4] = s_S.value();
     acc[5] = double(umax);
-    acc[6] = tot[5][t];
+    acc[6] = s_phit.value();
     acc[7] = double(bad);
-    acc[8] = tot[6][t];
+    acc[8] = s_int.value();
     acc[9] = 0.25 * double(quads);
     // block reduction: warp shuffles, then one warp over the warp results
     __shared__ double sm[LBM_NRED_DEV][32];

@@ -95,3 +95,13 @@ def test_full_lattice_droplet_count(full_run):
     assert s0["euler"] == float(len(geometry[1]))
     phi = out["phi"].cpu().numpy()
     assert s1["euler"] == float(measure.euler_characteristic(phi, (p.wall_x, False, p.wall_z)))
+
+
+def test_reduction_sums_carry_fp64_accuracy(full_run):
+    # the reduction forms each node's value in FP32 and sums it per thread as a float-float
+    # pair (about 1,200 nodes per thread at this size, error bound 1,200 * 2^-47 relative):
+    # its sum of phi over the whole lattice equals the FP64 sum of the same FP32 values
+    # (the fields' phi comes from the same phi pass) far below FP32's own rounding
+    _, _, out, _, s1, _ = full_run
+    ref = float(out["phi"].double().sum())
+    assert abs(s1["phi"] - ref) <= 1e-11 * abs(ref), (s1["phi"], ref)
