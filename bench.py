@@ -369,6 +369,19 @@ def gb300(args):
                           "roofline_frac": ALG_BYTES_PER_NODE["f32"] * nodes / (vms / vs / 1e3) / 1e9 / peak}
         del v
         torch.cuda.synchronize()
+        # the same in-place layout with FP16 storage (10.7 GB of state at 512^3)
+        q = p.with_(inplace=True, storage="f16")
+        v = Simulation(q, *init, device=device)
+        vs = max(20, args.steps // 2)
+        vms, vphi, vstep = time_device(v, vs, args.warmup, dist)
+        var["inplace_f16"] = {"value": ws * nodes * vs / (vms / 1e3) / 1e6, "unit": "MLUPS",
+                              "ms_per_step": vms / vs, "speedup_vs_f32": (ms / args.steps) / (vms / vs),
+                              "kernels": "phi_kernel + step_kernel (AA pattern, in place), FP16 storage",
+                              "phi_pass_ms": vphi, "step_kernel_ms": vstep, "state_gb": v.state.numel() / 1e9,
+                              "alg_bytes_per_node": ALG_BYTES_PER_NODE["f16"],
+                              "roofline_frac": ALG_BYTES_PER_NODE["f16"] * nodes / (vms / vs / 1e3) / 1e9 / peak}
+        del v
+        torch.cuda.synchronize()
         # the multiple-relaxation-time flow collision (D3Q19 moment basis), FP32 storage
         q = p.with_(collision="MRT")
         v = Simulation(q, *init, device=device)
