@@ -180,9 +180,9 @@ class LocalTransport:
 
 
 class DistTransport:
-    """One slab per rank of a torch.distributed group (rank i holds slab i). Two rounds of
+    """One slab per rank of a torch.distributed group (rank i holds slab i). Two exchanges of
     point-to-point messages, upward then downward, so that every pair of ranks exchanges at
-    most one message per direction per round (NCCL matches sends and receives by order)."""
+    most one message per direction per exchange (NCCL matches sends and receives by order)."""
 
     def __init__(self, wall_z, group=None):
         import torch.distributed as dist
@@ -197,8 +197,8 @@ class DistTransport:
         assert i == self.rank
         lower, upper = neighbours(i, self.n, self.wall_z)
         got = {}
-        # round 0: messages through upper faces (received at the neighbour's side 0);
-        # round 1: through lower faces (received at side 1)
+        # first exchange: messages through upper faces (received at the neighbour's side 0);
+        # second exchange: through lower faces (received at side 1)
         for send_side, nbr_to, nbr_from in ((1, upper, lower), (0, lower, upper)):
             recv_side = 1 - send_side
             if nbr_to == i:                                    # a single periodic slab
