@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 import torch
 
-from parity import TOL, rel_linf
+from parity import FLOORS, TOL, rel_linf
 from workloads import configs
 
 pytestmark = pytest.mark.gpu
@@ -105,3 +105,38 @@ def test_reduction_sums_carry_fp64_accuracy(full_run):
     _, _, out, _, s1, _ = full_run
     ref = float(out["phi"].double().sum())
     assert abs(s1["phi"] - ref) <= 1e-11 * abs(ref), (s1["phi"], ref)
+
+
+@pytest.mark.parametrize("inplace", [False, True], ids=["two_buffers", "in_place"])
+def test_fp16_storage_sampled_windows_match_oracle(full_run, inplace):
+    # the FP16-storage lines of the benchmark (fused two-buffer kernel, and the in-place
+    # layout) on the same 512^3 workload: the same sampled windows after the same two steps,
+    # held to the 16-bit bar. The scale of each field is its largest magnitude over all
+    # windows (a quiet bulk window alone would measure u against its own tiny values).
+    from oracle.lbm import OracleLBM
+    from paper_2409_03401_gb300 import Simulation
+    p, init, _, _, _, geometry = full_run
+    sim = Simulation(p.with_(storage="f16", inplace=inplace), *init)
+    sim.step(STEPS)
+    out = sim.fields()
+    torch.cuda.synchronize()
+    err, scale = {}, {}
+    for z0, y0, x0 in _corners(geometry):
+        z0 = min(max(z0, 0), N - WIN)
+        o = OracleLBM(p.with_(nx=WIN, ny=WIN, nz=WIN))
+        o.init(*[_window(t, z0, y0, x0, True) for t in init])
+        o.step(STEPS)
+        ref = o.fields()
+        zlo = 0 if z0 == 0 else MARGIN
+        zhi = WIN if z0 == N - WIN else WIN - MARGIN
+        sl = (slice(zlo, zhi), slice(MARGIN, WIN - MARGIN), slice(MARGIN, WIN - MARGIN))
+        for k in ("phi", "muA", "muB", "cA", "cB", "p", "ux", "uy", "uz"):
+            g = _window(out[k], z0, y0, x0, True)[sl].double()
+            r = ref[k][sl].double()
+            err[k] = max(err.get(k, 0.0), float((g - r).abs().max()))
+            scale[k] = max(scale.get(k, 0.0), float(r.abs().max()))
+    del sim, out
+    torch.cuda.synchronize()
+    rel = {k: err[k] / max(scale[k], FLOORS[k]) for k in err}
+    print(f"512^3 FP16 ({'in place' if inplace else 'two buffers'}) sampled-window errors:", rel)
+    assert all(v <= TOL["f16"] for v in rel.values()), rel
